@@ -1,0 +1,412 @@
+"""Pins of the FP64 oracle against what arXiv:1002.2184 and mathematics fix.
+
+None of these compare the oracle with itself: each expected value comes from
+the taps printed in Section II, the pair formulas of Fig. 4, a textbook
+closed form (the Haar basis functions), a polynomial identity, numpy's own
+convolution, or brute force on tiny inputs.  The mutation test at the end
+shows that a plausible mistake (wrong sign, transposed operand, wrong phase,
+dropped level, wrong scale) fails at least one pin.
+"""
+import math
+import types
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden
+from paper_1002_2184_gb300 import synth
+
+S = 1.0 / math.sqrt(2.0)
+
+
+def _taps_from_paper():
+    rows = {r[0]: np.array([float(v) for v in r[1:]]) for r in golden("paper_taps.txt")}
+    return rows["b0"], rows["b1"], rows["a0"], rows["a1"]
+
+
+def _matrix(fn, n):
+    """Columns are fn(e_i): the linear map as a dense matrix."""
+    cols = []
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        cols.append(np.asarray(fn(e)).ravel())
+    return np.stack(cols, axis=1)
+
+
+# --------------------------------------------------------------------------
+# Textbook Haar basis (independent closed form).  phi_l is the normalised box
+# of width 2^l; psi_l is -1 on its first half and +1 on its second half (the
+# high-pass sign of Eq. 9), both scaled by 2^(-l/2).
+# --------------------------------------------------------------------------
+
+def _phi(n, l, m):
+    v = np.zeros(n)
+    v[m << l:(m + 1) << l] = 2.0 ** (-l / 2)
+    return v
+
+
+def _psi(n, l, m):
+    v = np.zeros(n)
+    half = 1 << (l - 1)
+    v[m << l:(m << l) + half] = -(2.0 ** (-l / 2))
+    v[(m << l) + half:(m + 1) << l] = 2.0 ** (-l / 2)
+    return v
+
+
+def textbook_1d(n, levels):
+    rows = [None] * n
+    na = n >> levels
+    for m in range(na):
+        rows[m] = _phi(n, levels, m)
+    for l in range(levels, 0, -1):
+        nd = n >> l
+        for m in range(nd):
+            rows[nd + m] = _psi(n, l, m)
+    return np.stack(rows)
+
+
+def textbook_2d(h, w, levels):
+    B = np.zeros((h * w, h * w))
+
+    def put(r, c, vy, vx):
+        B[r * w + c] = np.outer(vy, vx).ravel()
+
+    hL, wL = h >> levels, w >> levels
+    for i in range(hL):
+        for j in range(wL):
+            put(i, j, _phi(h, levels, i), _phi(w, levels, j))
+    for l in range(1, levels + 1):
+        hl, wl = h >> l, w >> l
+        for i in range(hl):
+            for j in range(wl):
+                put(i, wl + j, _phi(h, l, i), _psi(w, l, j))       # Hx
+                put(hl + i, j, _psi(h, l, i), _phi(w, l, j))       # Hy
+                put(hl + i, wl + j, _psi(h, l, i), _psi(w, l, j))  # HH
+    return B
+
+
+# --------------------------------------------------------------------------
+# Pin checks, written against an implementation object so that mutants can
+# be run through them.  Each returns True when the pin holds.
+# --------------------------------------------------------------------------
+
+def pin_paper_pair_formulas(impl):
+    """Fig. 4 / Section II: one analysis stage on (x0, x1) is
+    d0 = (x0 + x1) s, d1 = (x1 - x0) s, with the printed analysis taps in
+    printed order weighting (x[2n], x[2n+1])."""
+    b0, b1, _, _ = _taps_from_paper()
+    rng = synth.rng(1, 0)
+    x = rng.standard_normal(64)
+    lo, hi = impl.analysis_1d(x)
+    pairs = x.reshape(-1, 2)
+    return (np.allclose(lo, pairs @ b0, rtol=0, atol=1e-14)
+            and np.allclose(hi, pairs @ b1, rtol=0, atol=1e-14))
+
+
+def pin_two_sample_matrix(impl):
+    """H2 = s [[1, 1], [-1, 1]]: det +1 (a rotation), orthogonal."""
+    M = _matrix(lambda e: np.concatenate(impl.analysis_1d(e)), 2)
+    H2 = S * np.array([[1.0, 1.0], [-1.0, 1.0]])
+    return (np.allclose(M, H2, atol=1e-15)
+            and abs(np.linalg.det(M) - 1.0) < 1e-14
+            and np.allclose(M @ M.T, np.eye(2), atol=1e-15))
+
+
+def pin_4pt_golden(impl):
+    G = np.array([[float(v) for v in r] for r in golden("haar_1d_4pt_2level.txt")])
+    M = _matrix(lambda e: impl.dwt1d(e, 2), 4)
+    return np.allclose(M, G, rtol=0, atol=1e-15)
+
+
+def pin_2x2_golden(impl):
+    G = np.array([[float(v) for v in r] for r in golden("haar_2d_2x2_butterfly.txt")])
+    M = _matrix(lambda e: impl.dwt2d(e.reshape(2, 2), 1).ravel(), 4)
+    return np.allclose(M, G, rtol=0, atol=1e-15)
+
+
+def pin_textbook_1d(impl):
+    for n, levels in [(2, 1), (8, 1), (8, 3), (16, 2), (32, 5), (64, 4)]:
+        M = _matrix(lambda e: impl.dwt1d(e, levels), n)
+        if not np.allclose(M, textbook_1d(n, levels), rtol=0, atol=1e-14):
+            return False
+    return True
+
+
+def pin_textbook_2d(impl):
+    for h, w, levels in [(2, 2, 1), (4, 4, 2), (8, 8, 3), (4, 8, 2), (8, 4, 1),
+                         (16, 8, 3)]:
+        M = _matrix(lambda e: impl.dwt2d(e.reshape(h, w), levels).ravel(), h * w)
+        if not np.allclose(M, textbook_2d(h, w, levels), rtol=0, atol=1e-14):
+            return False
+    return True
+
+
+def pin_constant_input(impl):
+    """A constant has zero detail at every level; the approximation grows by
+    sqrt(2) per level in 1D and by 2 per level in 2D."""
+    c = 0.3
+    for levels in (1, 3, 5):
+        y = impl.dwt1d(np.full(64, c), levels)
+        na = 64 >> levels
+        if np.any(y[na:] != 0.0):
+            return False
+        if not np.allclose(y[:na], c * 2.0 ** (levels / 2), rtol=1e-14, atol=0):
+            return False
+        z = impl.dwt2d(np.full((32, 64), c), levels)
+        mask = oracle.detail_mask_2d(32, 64, levels)
+        if np.any(z[mask] != 0.0):
+            return False
+        if not np.allclose(z[~mask], c * 2.0 ** levels, rtol=1e-14, atol=0):
+            return False
+    return True
+
+
+def pin_alternating_sign(impl):
+    """x[n] = (-1)^n is pure high frequency: d0 = 0 and d1 = -sqrt(2)
+    (d1 = (x[2n+1] - x[2n]) s with x[2n] = 1, x[2n+1] = -1)."""
+    x = np.array([1.0, -1.0] * 16)
+    lo, hi = impl.analysis_1d(x)
+    return (np.allclose(lo, 0.0, atol=1e-15)
+            and np.allclose(hi, -math.sqrt(2.0), rtol=1e-15, atol=0))
+
+
+def pin_parseval(impl):
+    rng = synth.rng(2, 0)
+    x1 = rng.standard_normal(1024)
+    x2 = rng.standard_normal((64, 128))
+    e1 = np.sum(impl.dwt1d(x1, 6) ** 2) / np.sum(x1 ** 2)
+    e2 = np.sum(impl.dwt2d(x2, 4) ** 2) / np.sum(x2 ** 2)
+    return abs(e1 - 1) < 1e-13 and abs(e2 - 1) < 1e-13
+
+
+PINS = [pin_paper_pair_formulas, pin_two_sample_matrix, pin_4pt_golden,
+        pin_2x2_golden, pin_textbook_1d, pin_textbook_2d, pin_constant_input,
+        pin_alternating_sign, pin_parseval]
+
+
+def _oracle_impl(detail_sign=1):
+    return types.SimpleNamespace(
+        analysis_1d=lambda x: oracle.analysis_1d(x, detail_sign),
+        dwt1d=lambda x, L: oracle.dwt1d(x, L, detail_sign),
+        dwt2d=lambda x, L: oracle.dwt2d(x, L, detail_sign),
+    )
+
+
+@pytest.mark.parametrize("pin", PINS, ids=lambda p: p.__name__)
+def test_pin_holds(pin):
+    assert pin(_oracle_impl())
+
+
+# --------------------------------------------------------------------------
+# Properties that need no implementation object.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,levels", [(2, 1), (64, 1), (64, 6), (1000, 3),
+                                      (4096, 12), (65536, 1)])
+def test_perfect_reconstruction_1d(n, levels):
+    x = synth.signal_1d(n, seed=7, index=n + levels)
+    y = oracle.idwt1d(oracle.dwt1d(x, levels), levels)
+    assert np.max(np.abs(y - x)) < 1e-13 * max(1.0, np.max(np.abs(x)))
+
+
+@pytest.mark.parametrize("h,w,levels", [(2, 2, 1), (8, 16, 3), (64, 32, 5),
+                                        (96, 160, 5), (256, 256, 8)])
+def test_perfect_reconstruction_2d(h, w, levels):
+    x = synth.piecewise_smooth_image(h, w, seed=11, index=h + w + levels)
+    y = oracle.idwt2d(oracle.dwt2d(x, levels), levels)
+    assert np.max(np.abs(y - x)) < 1e-14
+
+
+def test_synthesis_is_transpose_of_analysis():
+    """The bank is orthonormal (a_i are the time-reversed b_i, Section II):
+    the synthesis matrix equals the transpose of the analysis matrix."""
+    A = _matrix(lambda e: oracle.dwt2d(e.reshape(8, 8), 3).ravel(), 64)
+    Sy = _matrix(lambda e: oracle.idwt2d(e.reshape(8, 8), 3).ravel(), 64)
+    assert np.allclose(Sy, A.T, atol=1e-15)
+    assert np.allclose(A @ A.T, np.eye(64), atol=1e-14)
+
+
+def test_mallat_2d_is_not_kron():
+    """With two or more levels the Mallat 2D transform is not the tensor
+    product of two 1D transforms (it only recurses on LL)."""
+    A = _matrix(lambda e: oracle.dwt2d(e.reshape(4, 4), 2).ravel(), 16)
+    H4 = _matrix(lambda e: oracle.dwt1d(e, 2), 4)
+    assert not np.allclose(A, np.kron(H4, H4))
+    A1 = _matrix(lambda e: oracle.dwt2d(e.reshape(4, 4), 1).ravel(), 16)
+    assert np.allclose(A1, textbook_2d(4, 4, 1), atol=1e-15)
+
+
+def test_alias_cancellation_polynomials():
+    """Section II / Eq. 13-15: with the oracle's taps (read back by probing it
+    with impulses), A0(z)B0(-z) + A1(z)B1(-z) = 0 (alias term cancels) and
+    A0(z)B0(z) + A1(z)B1(z) = 2 z^-1 (distortion is a pure delay, undone by
+    taking the odd phase)."""
+    def analysis_taps(which):
+        # d_i[0] = y_i[1] = b_i[0] x[1] + b_i[1] x[0]
+        t0 = oracle.analysis_1d([0.0, 1.0])[which][0]
+        t1 = oracle.analysis_1d([1.0, 0.0])[which][0]
+        return np.array([t0, t1])
+
+    def synthesis_taps(which):
+        d = [[1.0], [0.0]] if which == 0 else [[0.0], [1.0]]
+        return oracle.synthesis_1d(d[0], d[1])
+
+    b0, b1 = analysis_taps(0), analysis_taps(1)
+    a0, a1 = synthesis_taps(0), synthesis_taps(1)
+    alt = np.array([1.0, -1.0])  # f(-z) for a 2-tap causal filter
+    alias = np.convolve(a0, b0 * alt) + np.convolve(a1, b1 * alt)
+    dist = np.convolve(a0, b0) + np.convolve(a1, b1)
+    assert np.allclose(alias, 0.0, atol=1e-15)
+    assert np.allclose(dist, [0.0, 2.0, 0.0], atol=1e-15)
+
+
+def test_definition_matches_numpy_convolution():
+    """Analysis = np.convolve with the causal taps, then the odd phase;
+    synthesis = zero insertion, np.convolve, sum, truncate."""
+    rng = synth.rng(3, 0)
+    x = rng.standard_normal(50)
+    b0, b1 = np.array([S, S]), np.array([S, -S])
+    a0, a1 = np.array([S, S]), np.array([-S, S])
+    lo, hi = oracle.analysis_1d(x)
+    assert np.allclose(lo, np.convolve(x, b0)[1::2][:25], atol=1e-15)
+    assert np.allclose(hi, np.convolve(x, b1)[1::2][:25], atol=1e-15)
+    u0 = np.zeros(50)
+    u1 = np.zeros(50)
+    u0[::2], u1[::2] = lo, hi
+    xr = (np.convolve(u0, a0) + np.convolve(u1, a1))[:50]
+    assert np.allclose(oracle.synthesis_1d(lo, hi), xr, atol=1e-15)
+
+
+def test_existing_vs_fast_haar():
+    """Section V compares the original bank with the fast one.  On the 1D
+    signal workload (2^16 samples) the definition and the polyphase form
+    agree to rounding; the error in dB (20 log10 of the relative L2 norm)
+    is far below the paper's -90 dB / -160 dB figures."""
+    x = synth.signal_1d(1 << 16)
+    lo, hi = oracle.analysis_1d(x)
+    plo, phi = oracle.polyphase_analysis_1d(x)
+    for a, b in ((lo, plo), (hi, phi)):
+        err = oracle.rel_l2(b, a)
+        assert err < 1e-15
+        assert 20 * math.log10(max(err, 1e-300)) < -250
+    xr = oracle.polyphase_synthesis_1d(plo, phi)
+    assert np.max(np.abs(xr - oracle.synthesis_1d(lo, hi))) < 1e-14
+    assert np.max(np.abs(xr - x)) < 1e-13
+
+
+def test_both_sign_conventions_reconstruct():
+    """detail_sign = -1 (the Section II taps read as causal) is also a
+    perfect-reconstruction bank; it only negates every detail."""
+    x = synth.signal_1d(256, seed=5)
+    c1 = oracle.dwt1d(x, 4, 1)
+    c2 = oracle.dwt1d(x, 4, -1)
+    na = 256 >> 4
+    assert np.allclose(c1[:na], c2[:na], atol=0)
+    assert np.allclose(c1[na:], -c2[na:], atol=0)
+    assert np.allclose(oracle.idwt1d(c2, 4, -1), x, atol=1e-13)
+
+
+@pytest.mark.parametrize("bad", [(6, 2), (10, 2), (8, 4)])
+def test_rejects_nondivisible(bad):
+    n, levels = bad
+    with pytest.raises(ValueError):
+        oracle.dwt1d(np.zeros(n), levels)
+    with pytest.raises(ValueError):
+        oracle.dwt2d(np.zeros((n, n)), levels)
+
+
+def test_empty_inputs():
+    assert oracle.dwt1d(np.zeros((0, 8)), 3).shape == (0, 8)
+    assert oracle.dwt2d(np.zeros((0, 4, 4)), 2).shape == (0, 4, 4)
+
+
+# --------------------------------------------------------------------------
+# Gradient of the denoising loss (the differentiation workload).
+# --------------------------------------------------------------------------
+
+def test_loss_gradient_matches_finite_differences():
+    rng = synth.rng(4, 0)
+    x = rng.standard_normal((2, 1, 8, 8)) * 0.2
+    t, lam, L = 0.05, 1e-3, 2
+    eps = 1e-6
+    c = oracle.dwt2d(x, L)
+    # a step of eps moves every coefficient by at most eps: stay off the kinks
+    assert np.min(np.abs(np.abs(c) - t)) > 10 * eps
+    g = oracle.denoise_loss_grad(x, L, t, lam)
+    fd = np.zeros_like(x)
+    for idx in np.ndindex(x.shape):
+        xp = x.copy()
+        xm = x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        fd[idx] = (oracle.denoise_loss(xp, L, t, lam)[0]
+                   - oracle.denoise_loss(xm, L, t, lam)[0]) / (2 * eps)
+    assert np.max(np.abs(g - fd)) < 1e-8
+
+
+def test_loss_limits():
+    """threshold 0 and no L1 term: the round trip is exact, loss and gradient
+    vanish.  Huge threshold: everything is zeroed, loss = mean(x^2) and the
+    gradient is 2x/n."""
+    rng = synth.rng(6, 0)
+    x = rng.standard_normal((1, 2, 16, 16))
+    loss, _, _ = oracle.denoise_loss(x, 3, 0.0, 0.0)
+    assert loss < 1e-28
+    assert np.max(np.abs(oracle.denoise_loss_grad(x, 3, 0.0, 0.0))) < 1e-15
+    loss, mse, l1 = oracle.denoise_loss(x, 3, 1e6, 1e-3)
+    assert l1 == 0.0 and abs(loss - np.mean(x ** 2)) < 1e-14
+    g = oracle.denoise_loss_grad(x, 3, 1e6, 1e-3)
+    assert np.allclose(g, 2 * x / x.size, atol=1e-16)
+
+
+# --------------------------------------------------------------------------
+# Mutation test: mistakes planted in (wrappers around) the oracle, on the
+# CPU, must each fail at least one pin.
+# --------------------------------------------------------------------------
+
+def _mutants():
+    base = _oracle_impl()
+    flipped = _oracle_impl(detail_sign=-1)
+
+    # the image handed over transposed (rows and columns swapped)
+    transposed = types.SimpleNamespace(
+        analysis_1d=base.analysis_1d, dwt1d=base.dwt1d,
+        dwt2d=lambda x, L: oracle.dwt2d(np.asarray(x).T, L)
+        if np.asarray(x).shape[0] == np.asarray(x).shape[1]
+        else oracle.dwt2d(x, L))
+
+    def wrong_phase_analysis(x):
+        return oracle.analysis_1d(np.roll(np.asarray(x, float), 1))
+
+    wrong_phase = types.SimpleNamespace(
+        analysis_1d=wrong_phase_analysis,
+        dwt1d=lambda x, L: oracle.dwt1d(np.roll(np.asarray(x, float), 1), L),
+        dwt2d=base.dwt2d)
+
+    dropped_level = types.SimpleNamespace(
+        analysis_1d=base.analysis_1d,
+        dwt1d=lambda x, L: oracle.dwt1d(x, max(L - 1, 1)),
+        dwt2d=lambda x, L: oracle.dwt2d(x, max(L - 1, 1)))
+
+    def scaled(x):
+        lo, hi = oracle.analysis_1d(x)
+        return lo * math.sqrt(2.0), hi
+
+    wrong_scale = types.SimpleNamespace(
+        analysis_1d=scaled,
+        dwt1d=base.dwt1d,
+        dwt2d=lambda x, L: oracle.dwt2d(x, L) * np.where(
+            oracle.detail_mask_2d(*np.asarray(x).shape, L), 1.0, 2.0))
+
+    return {"sign": flipped, "transposed": transposed, "phase": wrong_phase,
+            "dropped_level": dropped_level, "scale": wrong_scale}
+
+
+@pytest.mark.parametrize("name", ["sign", "transposed", "phase",
+                                  "dropped_level", "scale"])
+def test_planted_mistake_is_caught(name):
+    impl = _mutants()[name]
+    failed = [p.__name__ for p in PINS if not p(impl)]
+    assert failed, f"mutant {name} passed every pin"
