@@ -1,0 +1,494 @@
+"""Benchmark of the GB300 Fast Haar transform.
+
+Headline workload: one 4096 x 4096 fp32 piecewise-smooth image, 5-level 2D
+Fast Haar analysis followed by the full synthesis (DWT + IDWT round trip).
+One step = one round trip of one image.  The metric is input samples
+(pixels) per second through the round trip, in Gsamples/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  For N > 1 it is launched with
+torch.distributed.run, one process per GPU; the transform has no exchange
+step, so every rank runs an independent replica and the value is the sum of
+all ranks' samples over the slowest rank's time ("weak" scaling).
+
+``--impl reference`` times the FP64 CPU oracle (the plain definition of the
+filter bank) on the host cores instead, on a bounded crop of the same image
+per step; it runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Haar DWT+IDWT Gsamples/s & %HBM roofline; bf16/ragged/bwd vs plain fp32"
+UNIT = "Gsamples/s"
+N_SETS = 4  # rotating input/coefficient/output sets: 4 x 192 MB > L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--soak-s", type=float, default=1.5,
+                    help="seconds of untimed steps before the timed region (clocks settle)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (measurement only: no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(elapsed_ms: float, units: float, world: int, device=None):
+    """(max elapsed over ranks, sum of units over ranks)."""
+    if world == 1:
+        return elapsed_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the measurement
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1002_2184_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = kernel_source_hash()
+    for ln in lines:
+        if ln.startswith("#") or not ln.strip():
+            continue
+        kv = dict(p.split("=", 1) for p in ln.split() if "=" in p)
+        if kv.get("kernel") == kernel and kv.get("source_sha") == src:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1002_2184_gb300 import api, build, synth
+    build.build()
+
+    cfg = synth.Image2D()
+    H, W, L = cfg.h, cfg.w, cfg.levels
+    px = H * W
+    xs = [torch.from_numpy(synth.piecewise_smooth_image(H, W, cfg.seed, i).astype(np.float32))
+          .to(dev) for i in range(N_SETS)]
+    cs = [torch.empty_like(x) for x in xs]
+    ys = [torch.empty_like(x) for x in xs]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k):
+        s = k % N_SETS
+        api.dwt2d(xs[s], L, out=cs[s])
+        api.idwt2d(cs[s], L, out=ys[s])
+
+    for k in range(max(3, args.warmup)):
+        step(k)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(dev.index if world == 1 else local)
+    sampler.start()
+    t_end = time.time() + args.soak_s
+    k = 0
+    while time.time() < t_end:
+        step(k)
+        k += 1
+        if k % 64 == 0:
+            torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps, events around every kernel on the launching stream
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        s = k % N_SETS
+        ev[k][0].record(stream)
+        api.dwt2d(xs[s], L, out=cs[s])
+        ev[k][1].record(stream)
+        api.idwt2d(cs[s], L, out=ys[s])
+        ev[k][2].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    dwt_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    idwt_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+
+    max_ms, units = aggregate(elapsed_ms, float(px) * args.steps, world, dev)
+    value = units / (max_ms * 1e-3) / 1e9
+
+    # correctness guard on the timed data: the round trip reproduces the input
+    err = float(torch.linalg.vector_norm((ys[0] - xs[0]).double()) /
+                torch.linalg.vector_norm(xs[0].double()))
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    alg_bytes = 8.0 * px  # read 4 B + write 4 B per pixel, per kernel
+    dom = "k_dwt2d" if dwt_ms >= idwt_ms else "k_idwt2d"
+    dom_ms = max(dwt_ms, idwt_ms)
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+        "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_source": peak_src,
+        "traffic": recorded_traffic(dom),
+        "algorithmic_bytes_per_launch": alg_bytes,
+        "kernels": {
+            "k_dwt2d": {"avg_us": round(dwt_ms * 1e3, 2),
+                        "gbs": round(alg_bytes / (dwt_ms * 1e-3) / 1e9, 1)},
+            "k_idwt2d": {"avg_us": round(idwt_ms * 1e3, 2),
+                         "gbs": round(alg_bytes / (idwt_ms * 1e-3) / 1e9, 1)},
+        },
+    }
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"2D fp32 image {H}x{W}, {L}-level DWT then full IDWT",
+                   "h": H, "w": W, "levels": L, "batch_per_gpu": 1,
+                   "l2": f"rotating {N_SETS} input/coef/output sets "
+                         f"({N_SETS * 3 * px * 4 / 2**20:.0f} MiB) > L2; the IDWT reads the "
+                         "coefficients its DWT just wrote",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "gpu_launches": 2 * args.steps,
+        "round_trip_rel_l2": err,
+    }
+    if clocks:
+        out["clocks"] = clocks
+
+    if not args.no_e2e:
+        out["e2e"] = e2e_ours(api, synth, dev, cfg, min(args.steps, 20), world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_oracle(synth, cfg)
+    if not args.no_forms:
+        out["forms"] = forms(api, synth, dev, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_ours(api, synth, dev, cfg, steps, world):
+    """Same metric through the public API with host buffers: every step copies
+    the image from pinned host memory, runs DWT + IDWT, copies the result
+    back to pinned host memory."""
+    import torch
+    H, W, L = cfg.h, cfg.w, cfg.levels
+    host_in = torch.from_numpy(
+        synth.piecewise_smooth_image(H, W, cfg.seed, 0).astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    x = torch.empty(host_in.shape, dtype=torch.float32, device=dev)
+    c = torch.empty_like(x)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+
+    def one():
+        x.copy_(host_in, non_blocking=True)
+        api.dwt2d(x, L, out=c)
+        api.idwt2d(c, L, out=y)
+        host_out.copy_(y, non_blocking=True)
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms, units = aggregate(a.elapsed_time(b), float(H * W) * steps, world, dev)
+    ok = bool(torch.allclose(host_out, host_in, atol=1e-5))
+    return {"value": round(units / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": H * W * 4, "d2h_bytes_per_step": H * W * 4,
+            "steps": steps, "round_trip_ok": ok}
+
+
+def cpu_baseline_oracle(synth, cfg, min_seconds=10.0):
+    """The FP64 oracle as it stands, single-threaded, on this host: DWT + IDWT
+    of the full 4096 x 4096 image, repeated for about ``min_seconds``."""
+    import oracle
+    H, W, L = cfg.h, cfg.w, cfg.levels
+    x = synth.piecewise_smooth_image(H, W, cfg.seed, 0).astype(np.float32).astype(np.float64)
+    oracle.lib()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.idwt2d(oracle.dwt2d(x, L), L)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": round(H * W * reps / el / 1e9, 5), "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{reps} round trips of the full {H}x{W} image, {L} levels, "
+                      f"FP64 C oracle, one thread ({el:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# secondary forms, each next to the plain fp32 path on the same GPU
+# ---------------------------------------------------------------------------
+def time_ms(fn, iters, warmup=3):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(iters):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / iters
+
+
+def forms(api, synth, dev, world):
+    import torch
+    res = {}
+
+    # 1D signal, 2^16 samples, one level: launch-bound, reported as latency
+    sc = synth.Signal1D()
+    x1 = torch.from_numpy(synth.signal_1d(sc.n, sc.seed).astype(np.float32)).to(dev)
+    c1 = torch.empty_like(x1)
+    y1 = torch.empty_like(x1)
+
+    def sig():
+        api.dwt1d(x1, sc.levels, out=c1)
+        api.idwt1d(c1, sc.levels, out=y1)
+
+    ms = time_ms(sig, 200)
+    res["signal_1d"] = {"workload": f"1D fp32 signal n={sc.n}, {sc.levels} level, DWT+IDWT",
+                        "us_per_round_trip": round(ms * 1e3, 2),
+                        "gsamples_s": round(sc.n / (ms * 1e-3) / 1e9, 3),
+                        "note": "launch-latency bound; data resident in L2"}
+
+    # precision form: 64 x 2048^2, 4 levels; bf16 / fp16 / u8-in vs fp32
+    pc = synth.PrecisionBatch()
+    distinct = 8
+    base = np.stack([synth.piecewise_smooth_image(pc.h, pc.w, pc.seed, i)
+                     for i in range(distinct)])
+    x64 = torch.from_numpy(base).to(dev)
+    rep = pc.batch // distinct
+    xf = x64.float().repeat(rep, 1, 1)
+    px = pc.batch * pc.h * pc.w
+    entry = {"workload": f"{pc.batch} x {pc.h}x{pc.w} images ({distinct} distinct, repeated), "
+                         f"{pc.levels}-level 2D DWT+IDWT, FP32 arithmetic"}
+    for name, xdt, cdt, ydt in [("fp32", torch.float32, torch.float32, torch.float32),
+                                ("bf16", torch.bfloat16, torch.bfloat16, torch.bfloat16),
+                                ("fp16", torch.float16, torch.float16, torch.float16),
+                                ("u8_in_bf16_coef_fp32_out", torch.uint8, torch.bfloat16,
+                                 torch.float32)]:
+        if xdt == torch.uint8:
+            x = (xf.clamp(0, 1) * 255).round().to(torch.uint8)
+        else:
+            x = xf.to(xdt)
+        c = torch.empty(x.shape, dtype=cdt, device=dev)
+        y = torch.empty(x.shape, dtype=ydt, device=dev)
+
+        def rt():
+            api.dwt2d(x, pc.levels, out=c)
+            api.idwt2d(c, pc.levels, out=y)
+
+        ms = time_ms(rt, 5, warmup=2)
+        nbytes = px * (x.element_size() + 2 * c.element_size() + y.element_size())
+        entry[name] = {"ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
+                       "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1)}
+        del x, c, y
+    for name in ("bf16", "fp16", "u8_in_bf16_coef_fp32_out"):
+        entry[name]["speedup_vs_fp32"] = round(entry["fp32"]["ms"] / entry[name]["ms"], 3)
+    res["precision"] = entry
+    del xf, x64
+    torch.cuda.empty_cache()
+    return res
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1002_2184_gb300 import synth
+    import oracle
+    cfg = synth.Image2D()
+    H, W, L = cfg.h, cfg.w, cfg.levels
+    img = synth.piecewise_smooth_image(H, W, cfg.seed, 0).astype(np.float32).astype(np.float64)
+    # each step: DWT + IDWT of one 1024 x 1024 crop (a bounded sample)
+    side = 1024
+    crops = [img[i * side:(i + 1) * side, j * side:(j + 1) * side]
+             for i in range(H // side) for j in range(W // side)]
+    oracle.lib()
+    for k in range(args.warmup):
+        oracle.idwt2d(oracle.dwt2d(crops[k % len(crops)], L), L)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.idwt2d(oracle.dwt2d(crops[k % len(crops)], L), L)
+    el = time.perf_counter() - t0
+    value = side * side * args.steps / el / 1e9
+    sample = (f"each step: DWT+IDWT of one {side}x{side} crop of the {H}x{W} image, "
+              f"{L} levels, FP64 C oracle, one thread")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2D fp32 image {H}x{W}, {L}-level DWT then full IDWT",
+                   "h": H, "w": W, "levels": L, "batch_per_gpu": 1,
+                   "parallelism": "host CPU, one thread"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

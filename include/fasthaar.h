@@ -1,0 +1,144 @@
+/*
+ * fasthaar.h -- C ABI of the GB300 Fast Haar wavelet transform library
+ * (libfasthaar.so).
+ *
+ * The transform is the two-channel Haar filter bank of arXiv:1002.2184 in
+ * its polyphase ("Fast Haar") form: the down-sampler is moved in front of the
+ * filters (Section III, Eq. 8-12, Fig. 4) and the up-sampler behind them
+ * (Section IV, Eq. 17-19, Fig. 7), so each output pair is formed directly
+ * from one input pair and no decimated sample is ever computed:
+ *
+ *   analysis   d0[n] = (x[2n] + x[2n+1]) / sqrt(2)
+ *              d1[n] = (x[2n+1] - x[2n]) / sqrt(2)        (sign of Eq. 9)
+ *   synthesis  x[2n]   = (d0[n] - d1[n]) / sqrt(2)
+ *              x[2n+1] = (d0[n] + d1[n]) / sqrt(2)        (Eq. 19, Fig. 8)
+ *
+ * Multi-level transforms re-apply the bank to the low band (the paper's
+ * hierarchical decomposition, Section I) and store the result in the Mallat
+ * layout, with the same shape as the input:
+ *   1D: [a_L | d_L | d_{L-1} | ... | d_1] along each row;
+ *   2D: per level, rows then columns on the current LL region, quadrants
+ *       [LL | Hx] over [Hy | HH] (Hx: high pass along the width, low pass
+ *       along the height; Hy the reverse).  On one 2x2 block [[a, b], [c, d]]
+ *       this is LL = (a+b+c+d)/2, Hx = (b-a+d-c)/2, Hy = (c+d-a-b)/2,
+ *       HH = (a-b-c+d)/2.
+ *
+ * Conventions shared by every entry point:
+ *  - All data pointers are DEVICE pointers owned by the caller; the library
+ *    allocates no device memory.  Where a call needs scratch space it takes a
+ *    caller-provided workspace (size from haar_workspace_size).
+ *  - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *    stream); they never synchronise the device and may be captured into a
+ *    CUDA graph.
+ *  - Transforms are out of place.  Input and output ranges that overlap are
+ *    rejected with HAAR_EALIAS.
+ *  - Arithmetic is FP32 for fp32 / bf16 / fp16 / uint8 storage and FP64 for
+ *    fp64 storage.  Outputs are rounded to nearest-even into the output type.
+ *  - Extents must be divisible by 2^levels (no boundary extension): Haar
+ *    pairs never overlap, so none is needed.
+ *  - Errors are returned as negative status codes; nothing aborts, traps or
+ *    prints.  A CUDA error is returned as HAAR_ECUDA and its code is kept for
+ *    haar_last_cuda_error() (per host thread).
+ */
+#ifndef FASTHAAR_H
+#define FASTHAAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FASTHAAR_VERSION 1
+
+/* Status codes. */
+enum {
+  HAAR_OK = 0,
+  HAAR_EINVAL = -1,     /* null pointer, bad level count, negative extent or stride,
+                           mismatched shapes, nonzero reserved field */
+  HAAR_ESHAPE = -2,     /* a transformed extent is not divisible by 2^levels */
+  HAAR_EDTYPE = -3,     /* dtype (or dtype pair) not supported by this entry point */
+  HAAR_EALIAS = -4,     /* input and output memory ranges overlap */
+  HAAR_ECUDA = -5,      /* a CUDA runtime call failed; see haar_last_cuda_error() */
+  HAAR_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+  HAAR_EWORKSPACE = -7  /* workspace missing or smaller than haar_workspace_size() */
+};
+
+/* Storage types.  uint8 is accepted as analysis input only (values 0..255
+ * are transformed as they are, without scaling); fp64 pairs only with fp64
+ * and exists for gradient checks. */
+typedef enum {
+  HAAR_F32 = 0,
+  HAAR_BF16 = 1,
+  HAAR_F16 = 2,
+  HAAR_U8 = 3,
+  HAAR_F64 = 4
+} haar_dtype;
+
+/* A strided batch of 2D arrays.  Element (b, y, x) lives at
+ *   ptr + (b * batch_stride + y * row_stride + x) * sizeof(dtype).
+ * Rows are contiguous (unit column stride).  Strides are in ELEMENTS, must be
+ * non-negative, row_stride >= w when h > 1, and batch_stride must separate
+ * the items (batch_stride >= (h - 1) * row_stride + w when batch > 1).
+ * For 1D calls every row of every batch item is one independent signal of
+ * length w.  Any of batch, h, w may be 0 (nothing is done). */
+typedef struct {
+  void *ptr;
+  int32_t dtype;    /* haar_dtype */
+  int32_t reserved; /* must be 0 */
+  int64_t batch;
+  int64_t h;
+  int64_t w;
+  int64_t batch_stride;
+  int64_t row_stride;
+} haar_desc;
+
+/* Operation codes for haar_workspace_size. */
+enum { HAAR_OP_DWT_1D = 0, HAAR_OP_IDWT_1D = 1, HAAR_OP_DWT_2D = 2, HAAR_OP_IDWT_2D = 3 };
+
+/* Bytes of workspace the operation needs for this input descriptor and
+ * level count (0 when every level fuses into one kernel launch: up to 6
+ * levels in 2D, 12 in 1D).  Writes *bytes; returns a status. */
+int haar_workspace_size(int op, const haar_desc *src, int levels, size_t *bytes);
+
+/* 1D multi-level analysis (Fig. 4 per level) of every row of x into coef
+ * (Mallat layout along the row).  x and coef must have equal batch, h, w;
+ * w divisible by 2^levels; 1 <= levels <= 62.
+ * dtypes: x in {F32, BF16, F16, U8}, coef in {F32, BF16, F16}; or both F64.
+ * workspace: device memory of at least haar_workspace_size(HAAR_OP_DWT_1D)
+ * bytes (may be NULL when that size is 0), 256-byte aligned. */
+int haar_dwt_1d(const haar_desc *x, const haar_desc *coef, int levels, void *workspace,
+                size_t workspace_bytes, void *cuda_stream);
+
+/* 1D multi-level synthesis (Eq. 19 per level, coarsest first): inverse of
+ * haar_dwt_1d.  dtypes: coef and x in {F32, BF16, F16}; or both F64. */
+int haar_idwt_1d(const haar_desc *coef, const haar_desc *x, int levels, void *workspace,
+                 size_t workspace_bytes, void *cuda_stream);
+
+/* 2D multi-level separable analysis of every h x w image of x into coef
+ * (Mallat quadrant layout).  h and w divisible by 2^levels.  Up to 6 levels
+ * run fused in one launch; deeper transforms chain launches through the
+ * workspace.  dtypes as haar_dwt_1d. */
+int haar_dwt_2d(const haar_desc *x, const haar_desc *coef, int levels, void *workspace,
+                size_t workspace_bytes, void *cuda_stream);
+
+/* 2D multi-level synthesis, coarsest level first: inverse of haar_dwt_2d.
+ * dtypes as haar_idwt_1d. */
+int haar_idwt_2d(const haar_desc *coef, const haar_desc *x, int levels, void *workspace,
+                 size_t workspace_bytes, void *cuda_stream);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *haar_status_string(int status);
+
+/* The cudaError_t of the last HAAR_ECUDA returned on this host thread. */
+int haar_last_cuda_error(void);
+
+/* FASTHAAR_VERSION of the loaded library. */
+int haar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTHAAR_H */

@@ -1,0 +1,138 @@
+"""PyTorch-facing calls into libfasthaar: tensors in, tensors out.
+
+These functions only describe tensors to the C ABI (pointer, dtype, extents,
+strides) and pass torch's current CUDA stream; the transforms run in the
+library's kernels.  Inputs must be CUDA tensors whose rows are contiguous and
+whose leading dimensions flatten to one batch stride.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import torch
+
+from . import _lib
+
+_DTYPES = {
+    torch.float32: _lib.HAAR_F32,
+    torch.bfloat16: _lib.HAAR_BF16,
+    torch.float16: _lib.HAAR_F16,
+    torch.uint8: _lib.HAAR_U8,
+    torch.float64: _lib.HAAR_F64,
+}
+
+
+def haar_dtype(dt: torch.dtype) -> int:
+    try:
+        return _DTYPES[dt]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {dt}") from None
+
+
+def _lead_stride(t: torch.Tensor, nlead: int, inner: int) -> Tuple[int, int]:
+    """(count, stride) of the first ``nlead`` dims flattened into one; raises
+    if they are not evenly strided."""
+    count, stride = 1, None
+    for d in range(nlead - 1, -1, -1):
+        n, s = t.shape[d], t.stride(d)
+        if n == 1:
+            continue
+        if stride is None:
+            stride = s
+            expect = s * n
+        else:
+            if s != expect:
+                raise ValueError("leading dimensions do not flatten to one batch stride; "
+                                 "pass a contiguous tensor")
+            expect = s * n
+        count *= n
+    return count, (stride if stride is not None else inner)
+
+
+def describe(t: torch.Tensor, one_d: bool = False) -> _lib.HaarDesc:
+    """The haar_desc of a tensor: (..., h, w) for 2D; (..., w) for 1D, where
+    every row is one signal."""
+    if not t.is_cuda:
+        raise ValueError("libfasthaar works on CUDA tensors only")
+    if t.dim() < 1 or (not one_d and t.dim() < 2):
+        raise ValueError("tensor has too few dimensions")
+    if t.numel() and t.shape[-1] > 1 and t.stride(-1) != 1:
+        raise ValueError("rows must be contiguous (last stride 1)")
+    w = t.shape[-1]
+    if t.dim() == 1:
+        h, rs, batch, bs = 1, w, 1, w
+    else:
+        h, rs = t.shape[-2], t.stride(-2)
+        if h == 1:
+            rs = w
+        batch, bs = _lead_stride(t, t.dim() - 2, h * rs)
+    return _lib.desc(t.data_ptr(), haar_dtype(t.dtype), batch, h, w, bs, rs)
+
+
+def _stream(t: torch.Tensor) -> int:
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def workspace_size(op: int, d: _lib.HaarDesc, levels: int) -> int:
+    lib = _lib.load()
+    n = ctypes.c_size_t(0)
+    _lib.check(lib.haar_workspace_size(op, ctypes.byref(d), levels, ctypes.byref(n)),
+               "haar_workspace_size")
+    return n.value
+
+
+def _run(fn_name: str, op: int, src: torch.Tensor, dst: torch.Tensor, levels: int,
+         one_d: bool) -> torch.Tensor:
+    lib = _lib.load()
+    ds, dd = describe(src, one_d), describe(dst, one_d)
+    nbytes = workspace_size(op, ds, levels)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=src.device) if nbytes else None
+    with torch.cuda.device(src.device):
+        rc = getattr(lib, fn_name)(ctypes.byref(ds), ctypes.byref(dd), levels,
+                                   ws.data_ptr() if ws is not None else None, nbytes,
+                                   _stream(src))
+    _lib.check(rc, fn_name)
+    return dst
+
+
+def _out_like(x: torch.Tensor, dtype: torch.dtype, out: Optional[torch.Tensor]) -> torch.Tensor:
+    if out is None:
+        return torch.empty(x.shape, dtype=dtype, device=x.device)
+    if out.shape != x.shape:
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {tuple(x.shape)}")
+    return out
+
+
+def _coef_dtype(x: torch.Tensor, dtype: Optional[torch.dtype]) -> torch.dtype:
+    if dtype is not None:
+        return dtype
+    return torch.float32 if x.dtype == torch.uint8 else x.dtype
+
+
+def dwt2d(x: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
+          dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """Multi-level 2D Fast Haar analysis of (..., h, w) into the Mallat layout."""
+    out = _out_like(x, _coef_dtype(x, dtype) if out is None else out.dtype, out)
+    return _run("haar_dwt_2d", _lib.HAAR_OP_DWT_2D, x, out, levels, False)
+
+
+def idwt2d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
+           dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """Inverse of :func:`dwt2d`."""
+    out = _out_like(c, (dtype or c.dtype) if out is None else out.dtype, out)
+    return _run("haar_idwt_2d", _lib.HAAR_OP_IDWT_2D, c, out, levels, False)
+
+
+def dwt1d(x: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
+          dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """Multi-level 1D Fast Haar analysis of every row of (..., n)."""
+    out = _out_like(x, _coef_dtype(x, dtype) if out is None else out.dtype, out)
+    return _run("haar_dwt_1d", _lib.HAAR_OP_DWT_1D, x, out, levels, True)
+
+
+def idwt1d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
+           dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """Inverse of :func:`dwt1d`."""
+    out = _out_like(c, (dtype or c.dtype) if out is None else out.dtype, out)
+    return _run("haar_idwt_1d", _lib.HAAR_OP_IDWT_1D, c, out, levels, True)

@@ -1,0 +1,30 @@
+// Launchers for float input storage (all fp output types).
+#include "haar_launch.cuh"
+
+namespace fh {
+
+cudaError_t launch_dwt2d_f32(int tout, Pass p, int cfg, bool vec, int cap, cudaStream_t s) {
+  FH_TOUT_SWITCH_FLOATS((dwt2d_t<float, float>(p, cfg, vec, cap, s)),
+                        (dwt2d_t<float, __nv_bfloat16>(p, cfg, vec, cap, s)),
+                        (dwt2d_t<float, __half>(p, cfg, vec, cap, s)))
+}
+
+cudaError_t launch_idwt2d_f32(int tout, Pass p, int cfg, bool vec, int cap, cudaStream_t s) {
+  FH_TOUT_SWITCH_FLOATS((idwt2d_t<float, float>(p, cfg, vec, cap, s)),
+                        (idwt2d_t<float, __nv_bfloat16>(p, cfg, vec, cap, s)),
+                        (idwt2d_t<float, __half>(p, cfg, vec, cap, s)))
+}
+
+cudaError_t launch_dwt1d_f32(int tout, Pass p, int cfg, bool vec, cudaStream_t s) {
+  FH_TOUT_SWITCH_FLOATS((dwt1d_t<float, float>(p, cfg, vec, s)),
+                        (dwt1d_t<float, __nv_bfloat16>(p, cfg, vec, s)),
+                        (dwt1d_t<float, __half>(p, cfg, vec, s)))
+}
+
+cudaError_t launch_idwt1d_f32(int tout, Pass p, int cfg, bool vec, cudaStream_t s) {
+  FH_TOUT_SWITCH_FLOATS((idwt1d_t<float, float>(p, cfg, vec, s)),
+                        (idwt1d_t<float, __nv_bfloat16>(p, cfg, vec, s)),
+                        (idwt1d_t<float, __half>(p, cfg, vec, s)))
+}
+
+}  // namespace fh

@@ -1,0 +1,129 @@
+"""The C ABI library loads and exports every entry point its header declares,
+and rejects bad arguments on the host before any device work (no GPU needed:
+these calls fail validation, so nothing is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "fasthaar.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(haar_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1002_2184_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("haar_dwt_1d", "haar_idwt_1d", "haar_dwt_2d", "haar_idwt_2d",
+              "haar_workspace_size", "haar_status_string"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_1002_2184_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_version_and_strings(lib):
+    assert lib.haar_version() == 1
+    for s in range(0, -8, -1):
+        assert lib.haar_status_string(s) not in (None, b"", b"unknown status")
+    assert lib.haar_status_string(-99) == b"unknown status"
+
+
+# ---------------------------------------------------------------------------
+# Host-side validation (T11).  Fake, never-dereferenced device addresses.
+# ---------------------------------------------------------------------------
+A = 1 << 40          # fake device address, 256-byte aligned
+B = A + (1 << 30)    # far away from A
+
+
+def d(ptr, dt=0, b=1, h=8, w=8, bs=None, rs=None):
+    from paper_1002_2184_gb300 import _lib
+    rs = w if rs is None else rs
+    bs = h * rs if bs is None else bs
+    return _lib.desc(ptr, dt, b, h, w, bs, rs)
+
+
+def call(lib, name, src, dst, levels, ws=None, wsb=0):
+    return getattr(lib, name)(ctypes.byref(src), ctypes.byref(dst), levels, ws, wsb, None)
+
+
+@pytest.mark.parametrize("name", ["haar_dwt_2d", "haar_idwt_2d", "haar_dwt_1d", "haar_idwt_1d"])
+def test_rejections(lib, name):
+    from paper_1002_2184_gb300 import _lib as L
+    two_d = name.endswith("2d")
+    # level count
+    assert call(lib, name, d(A), d(B), 0) == L.HAAR_EINVAL
+    assert call(lib, name, d(A), d(B), 63) == L.HAAR_EINVAL
+    # not divisible by 2^levels
+    assert call(lib, name, d(A, w=12), d(B, w=12), 3) == L.HAAR_ESHAPE
+    if two_d:
+        assert call(lib, name, d(A, h=12), d(B, h=12), 3) == L.HAAR_ESHAPE
+    # null pointer with data
+    assert call(lib, name, d(0), d(B), 1) == L.HAAR_EINVAL
+    # shape mismatch
+    assert call(lib, name, d(A), d(B, w=16), 1) == L.HAAR_EINVAL
+    # overlapping input and output
+    assert call(lib, name, d(A), d(A + 16), 1) == L.HAAR_EALIAS
+    # negative or too-small strides
+    assert call(lib, name, d(A, rs=4), d(B), 1) == L.HAAR_EINVAL
+    assert call(lib, name, d(A, b=2, bs=8), d(B, b=2), 1) == L.HAAR_EINVAL
+    # reserved field
+    bad = d(A)
+    bad.reserved = 1
+    assert call(lib, name, bad, d(B), 1) == L.HAAR_EINVAL
+    # unknown dtype
+    assert call(lib, name, d(A, dt=9), d(B), 1) == L.HAAR_EDTYPE
+    # fp64 only pairs with fp64
+    assert call(lib, name, d(A, dt=4), d(B, dt=0), 1) == L.HAAR_EDTYPE
+    # uint8 is never an output
+    assert call(lib, name, d(A), d(B, dt=3), 1) == L.HAAR_EDTYPE
+    # empty input: nothing to do, success without touching the device
+    assert call(lib, name, d(A, b=0), d(B, b=0), 3) == L.HAAR_OK
+    assert call(lib, name, d(0, h=0), d(0, h=0), 3) == L.HAAR_OK
+
+
+def test_uint8_only_as_analysis_input(lib):
+    from paper_1002_2184_gb300 import _lib as L
+    assert call(lib, "haar_idwt_2d", d(A, dt=3), d(B), 1) == L.HAAR_EDTYPE
+    assert call(lib, "haar_idwt_1d", d(A, dt=3), d(B), 1) == L.HAAR_EDTYPE
+
+
+def test_workspace_sizes(lib):
+    from paper_1002_2184_gb300 import _lib as L
+    n = ctypes.c_size_t()
+    src = d(A, h=4096, w=4096)
+    for op in (L.HAAR_OP_DWT_2D, L.HAAR_OP_IDWT_2D):
+        assert lib.haar_workspace_size(op, ctypes.byref(src), 6, ctypes.byref(n)) == 0
+        assert n.value == 0  # six levels fuse into one launch
+        assert lib.haar_workspace_size(op, ctypes.byref(src), 7, ctypes.byref(n)) == 0
+        assert n.value == 64 * 64 * 4  # LL after 6 levels, fp32
+    src1 = d(A, h=3, w=1 << 20)
+    assert lib.haar_workspace_size(L.HAAR_OP_DWT_1D, ctypes.byref(src1), 12,
+                                   ctypes.byref(n)) == 0 and n.value == 0
+    assert lib.haar_workspace_size(L.HAAR_OP_DWT_1D, ctypes.byref(src1), 20,
+                                   ctypes.byref(n)) == 0 and n.value == 3 * 256 * 4
+    # a deep transform refuses a missing or short workspace
+    assert call(lib, "haar_dwt_2d", src, d(B, h=4096, w=4096), 7) == L.HAAR_EWORKSPACE
+    assert call(lib, "haar_dwt_2d", src, d(B, h=4096, w=4096), 7,
+                ws=1 << 41, wsb=100) == L.HAAR_EWORKSPACE
+    assert lib.haar_workspace_size(9, ctypes.byref(src), 1, ctypes.byref(n)) == L.HAAR_EINVAL

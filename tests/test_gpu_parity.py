@@ -1,0 +1,228 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over the whole output, plus an element-wise bound
+relative to the largest reference magnitude):
+  fp32 storage: rel-L2 <= 1e-6, max-abs <= 4e-6 * max|ref|
+  bf16 storage: rel-L2 <= 1e-2, max-abs <= 2^-7 * max|ref|
+  fp16 storage: rel-L2 <= 2e-3, max-abs <= 2^-9 * max|ref|
+  fp64 storage: rel-L2 <= 1e-13
+The oracle always receives exactly the values the GPU read (inputs are cast
+to the storage type first, then widened back to float64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1002_2184_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+TOL = {
+    torch.float32: (1e-6, 4e-6),
+    torch.bfloat16: (1e-2, 2.0 ** -7),
+    torch.float16: (2e-3, 2.0 ** -9),
+    torch.float64: (1e-13, 1e-13),
+}
+
+
+def assert_close(gpu, ref, dtype, what=""):
+    got = gpu.detach().double().cpu().numpy()
+    rel_tol, abs_tol = TOL[dtype]
+    err = oracle.rel_l2(got, ref)
+    scale = float(np.max(np.abs(ref))) if ref.size else 0.0
+    mx = oracle.max_abs(got, ref)
+    assert err <= rel_tol, f"{what}: rel-L2 {err:.3e} > {rel_tol:.1e}"
+    assert mx <= abs_tol * max(scale, 1e-30), f"{what}: max-abs {mx:.3e} (scale {scale:.3e})"
+    return err, mx
+
+
+def dev(a: np.ndarray, dtype) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dtype)
+
+
+def host64(t: torch.Tensor) -> np.ndarray:
+    return t.detach().double().cpu().numpy()
+
+
+def images(batch, h, w, seed=0):
+    return np.stack([synth.piecewise_smooth_image(h, w, seed=seed, index=i)
+                     for i in range(batch)])
+
+
+# ---------------------------------------------------------------------------
+# 2D
+# ---------------------------------------------------------------------------
+CASES_2D = [
+    (1, 2, 2, 1),        # smallest image
+    (1, 8, 8, 3),        # full depth of a tiny image
+    (2, 64, 64, 6),      # one 64x128 tile, partly filled
+    (1, 96, 160, 5),     # ragged tail in both directions
+    (3, 32, 256, 5),     # several tiles per row, batch of 3
+    (1, 128, 64, 6),     # tall image
+    (1, 256, 512, 8),    # two chained passes (6 + 2 levels)
+    (1, 1024, 1024, 10),
+    (2, 192, 320, 1),    # one level
+    (1, 48, 40, 3),      # w % 8 != 0 -> scalar path
+]
+
+
+@pytest.mark.parametrize("b,h,w,levels", CASES_2D)
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16, torch.float16])
+def test_dwt2d_matches_oracle(b, h, w, levels, dt):
+    x = dev(images(b, h, w, seed=h * 7 + w), dt)
+    c = api.dwt2d(x, levels)
+    assert c.dtype == dt
+    ref = oracle.dwt2d(host64(x), levels)
+    assert_close(c, ref, dt, f"dwt2d {b}x{h}x{w} L{levels} {dt}")
+
+
+@pytest.mark.parametrize("b,h,w,levels", CASES_2D)
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16, torch.float16])
+def test_idwt2d_matches_oracle(b, h, w, levels, dt):
+    x = images(b, h, w, seed=h * 5 + w)
+    c = dev(oracle.dwt2d(x, levels), dt)
+    y = api.idwt2d(c, levels)
+    ref = oracle.idwt2d(host64(c), levels)
+    assert_close(y, ref, dt, f"idwt2d {b}x{h}x{w} L{levels} {dt}")
+
+
+@pytest.mark.parametrize("b,h,w,levels", CASES_2D)
+def test_round_trip_2d_fp32(b, h, w, levels):
+    x = dev(images(b, h, w, seed=3), torch.float32)
+    y = api.idwt2d(api.dwt2d(x, levels), levels)
+    assert oracle.rel_l2(host64(y), host64(x)) <= 1e-6
+
+
+def test_image_workload_full_size():
+    """4096 x 4096 fp32, 5 levels: every coefficient and every reconstructed
+    pixel against the oracle."""
+    cfg = synth.Image2D()
+    xn = synth.piecewise_smooth_image(cfg.h, cfg.w, cfg.seed).astype(np.float32)
+    x = dev(xn, torch.float32)
+    c = api.dwt2d(x, cfg.levels)
+    ref = oracle.dwt2d(xn.astype(np.float64), cfg.levels)
+    assert_close(c, ref, torch.float32, "dwt2d 4096^2 L5")
+    y = api.idwt2d(c, cfg.levels)
+    assert_close(y, oracle.idwt2d(host64(c), cfg.levels), torch.float32, "idwt2d 4096^2 L5")
+    assert oracle.rel_l2(host64(y), xn) <= 1e-6
+
+
+@pytest.mark.parametrize("levels", [7, 12])
+def test_deep_2d_chained_passes(levels):
+    x = dev(images(1, 4096, 4096, seed=levels), torch.float32)
+    c = api.dwt2d(x, levels)
+    ref = oracle.dwt2d(host64(x), levels)
+    assert_close(c, ref, torch.float32, f"dwt2d 4096^2 L{levels}")
+    y = api.idwt2d(c, levels)
+    assert_close(y, oracle.idwt2d(host64(c), levels), torch.float32, f"idwt2d L{levels}")
+
+
+def test_strided_and_offset_views():
+    """Views with row_stride > w and batch_stride > h*row_stride; an offset
+    of 8 elements keeps the vector path, an offset of 1 forces the scalar
+    path."""
+    base = dev(images(2, 80, 200, seed=9), torch.float32)
+    for off in (8, 1):
+        x = base[:, 8:72, off:off + 128]
+        assert x.stride(-2) == 200
+        c = torch.empty((2, 64, 160), device=DEV)[:, :, 16:144]
+        api.dwt2d(x, 4, out=c)
+        assert_close(c, oracle.dwt2d(host64(x), 4), torch.float32, f"strided off={off}")
+        y = api.idwt2d(c, 4)
+        assert oracle.rel_l2(host64(y), host64(x)) <= 1e-6
+
+
+def test_uint8_input():
+    xn = synth.quantize_u8(images(2, 128, 256, seed=4))
+    x = torch.from_numpy(xn).to(DEV)
+    for dt in (torch.float32, torch.bfloat16):
+        c = api.dwt2d(x, 4, dtype=dt)
+        assert_close(c, oracle.dwt2d(xn.astype(np.float64), 4), dt, f"u8 -> {dt}")
+
+
+def test_fp64_path():
+    x = dev(images(2, 64, 128, seed=5), torch.float64)
+    c = api.dwt2d(x, 6)
+    assert_close(c, oracle.dwt2d(host64(x), 6), torch.float64, "fp64 dwt2d")
+    y = api.idwt2d(c, 6)
+    assert np.max(np.abs(host64(y) - host64(x))) < 1e-14
+
+
+def test_constant_image_has_exact_zero_detail():
+    """A constant image gives exactly zero detail in fp32 (x1 - x0 = 0) and
+    LL_L = 2^L c exactly for c a power of two."""
+    x = torch.full((1, 256, 512), 0.25, device=DEV)
+    c = host64(api.dwt2d(x, 6))[0]
+    mask = oracle.detail_mask_2d(256, 512, 6)
+    assert np.all(c[mask] == 0.0)
+    assert np.all(c[~mask] == 0.25 * 64)
+
+
+def test_impulse_responses_match_oracle_columns():
+    """W e_i for every pixel i of a 16 x 32 image (L = 3): the GPU's linear
+    map equals the oracle's, column by column."""
+    h, w, L = 16, 32, 3
+    eye = torch.eye(h * w, device=DEV).reshape(h * w, h, w)
+    cols = host64(api.dwt2d(eye, L)).reshape(h * w, h * w).T
+    ref = np.stack([oracle.dwt2d(np.eye(h * w)[i].reshape(h, w), L).ravel()
+                    for i in range(h * w)], axis=1)
+    assert np.max(np.abs(cols - ref)) < 1e-7
+
+
+# ---------------------------------------------------------------------------
+# 1D
+# ---------------------------------------------------------------------------
+CASES_1D = [
+    (1, 1, 2, 1),
+    (1, 1, 8, 3),
+    (1, 1, 65536, 1),        # the signal workload
+    (2, 3, 3112, 3),         # ragged chunk tail, batch x rows
+    (1, 4, 1024, 10),
+    (1, 1, 4096 + 8, 3),
+    (1, 2, 1 << 20, 16),     # two chained passes (12 + 4)
+    (1, 1, 1000, 3),         # n % 8 != 0 -> scalar path
+]
+
+
+@pytest.mark.parametrize("b,r,n,levels", CASES_1D)
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16, torch.float16])
+def test_dwt1d_matches_oracle(b, r, n, levels, dt):
+    xs = np.stack([synth.signal_1d(n, seed=n, index=i) for i in range(b * r)]).reshape(b, r, n)
+    x = dev(xs, dt)
+    c = api.dwt1d(x, levels)
+    assert_close(c, oracle.dwt1d(host64(x), levels), dt, f"dwt1d {b}x{r}x{n} L{levels}")
+    y = api.idwt1d(c, levels)
+    assert_close(y, oracle.idwt1d(host64(c), levels), dt, f"idwt1d {b}x{r}x{n} L{levels}")
+    if dt == torch.float32:
+        assert oracle.rel_l2(host64(y), host64(x)) <= 1e-6
+
+
+def test_signal_workload_round_trip():
+    cfg = synth.Signal1D()
+    xn = synth.signal_1d(cfg.n, cfg.seed).astype(np.float32)
+    x = dev(xn, torch.float32)
+    c = api.dwt1d(x, cfg.levels)
+    assert_close(c, oracle.dwt1d(xn.astype(np.float64), cfg.levels), torch.float32, "signal")
+    y = api.idwt1d(c, cfg.levels)
+    assert oracle.rel_l2(host64(y), xn) <= 1e-6
+    lo, hi = oracle.polyphase_analysis_1d(xn.astype(np.float64))
+    got = host64(c)
+    assert oracle.rel_l2(got[:cfg.n // 2], lo) <= 1e-6
+    assert oracle.rel_l2(got[cfg.n // 2:], hi) <= 1e-6
+
+
+def test_1d_fp64_and_u8():
+    x = dev(synth.signal_1d(4096, seed=1), torch.float64)
+    c = api.dwt1d(x, 12)
+    assert_close(c, oracle.dwt1d(host64(x), 12), torch.float64, "fp64 dwt1d")
+    u = torch.from_numpy(synth.quantize_u8(synth.signal_1d(2048, seed=2) * 0.2 + 0.5)).to(DEV)
+    cu = api.dwt1d(u, 5)
+    assert_close(cu, oracle.dwt1d(host64(u), 5), torch.float32, "u8 dwt1d")
+
+
+def test_empty_tensors():
+    x = torch.empty((0, 64, 64), device=DEV)
+    assert api.dwt2d(x, 3).shape == (0, 64, 64)
+    assert api.idwt1d(torch.empty((3, 0), device=DEV), 2).shape == (3, 0)
