@@ -136,3 +136,55 @@ def idwt1d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
     """Inverse of :func:`dwt1d`."""
     out = _out_like(c, (dtype or c.dtype) if out is None else out.dtype, out)
     return _run("haar_idwt_1d", _lib.HAAR_OP_IDWT_1D, c, out, levels, True)
+
+
+class Plan:
+    """A transform bound to fixed tensors: descriptors, level count and
+    workspace are prepared once, so each call is a single C-ABI call with no
+    allocation (safe to capture into a CUDA graph).
+
+    ``Plan(x, coef, levels, y=None, one_d=False)`` plans x -> coef (analysis)
+    and, when ``y`` is given, coef -> y (synthesis).
+    """
+
+    def __init__(self, x: torch.Tensor, coef: torch.Tensor, levels: int,
+                 y: Optional[torch.Tensor] = None, one_d: bool = False):
+        self.lib = _lib.load()
+        self.levels = int(levels)
+        self.device = x.device
+        self._keep = (x, coef, y)
+        self._dx = describe(x, one_d)
+        self._dc = describe(coef, one_d)
+        self._dy = describe(y, one_d) if y is not None else None
+        if one_d:
+            ops = (_lib.HAAR_OP_DWT_1D, _lib.HAAR_OP_IDWT_1D)
+            self._fwd, self._inv = self.lib.haar_dwt_1d, self.lib.haar_idwt_1d
+        else:
+            ops = (_lib.HAAR_OP_DWT_2D, _lib.HAAR_OP_IDWT_2D)
+            self._fwd, self._inv = self.lib.haar_dwt_2d, self.lib.haar_idwt_2d
+        n = max(workspace_size(ops[0], self._dx, self.levels),
+                workspace_size(ops[1], self._dc, self.levels))
+        self._ws = torch.empty(n, dtype=torch.uint8, device=x.device) if n else None
+        self._ws_ptr = self._ws.data_ptr() if n else None
+        self._ws_n = n
+        self._px, self._pc = ctypes.byref(self._dx), ctypes.byref(self._dc)
+        self._py = ctypes.byref(self._dy) if y is not None else None
+
+    def _stream(self, stream) -> int:
+        if stream is None:
+            return torch.cuda.current_stream(self.device).cuda_stream
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def dwt(self, stream=None) -> None:
+        rc = self._fwd(self._px, self._pc, self.levels, self._ws_ptr, self._ws_n,
+                       self._stream(stream))
+        if rc:
+            _lib.check(rc, "dwt")
+
+    def idwt(self, stream=None) -> None:
+        if self._py is None:
+            raise ValueError("plan has no synthesis output")
+        rc = self._inv(self._pc, self._py, self.levels, self._ws_ptr, self._ws_n,
+                       self._stream(stream))
+        if rc:
+            _lib.check(rc, "idwt")

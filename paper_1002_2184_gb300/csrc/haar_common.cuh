@@ -13,6 +13,38 @@
 namespace fh {
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel is launched with programmatic
+// stream serialisation allowed, so the next kernel in the stream can be
+// scheduled while this one drains.  pdl_wait() blocks until all prerequisite
+// grids have completed and their memory is visible; every kernel calls it
+// before its first global memory access, so ordering is exactly that of
+// plain stream order.  pdl_trigger() lets the next grid begin launching.
+// Both are no-ops for a grid launched without the attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `kernel<<<grid, block, 0, stream>>>(arg)` with programmatic stream
+// serialisation allowed (see pdl_wait).
+template <typename Arg>
+inline cudaError_t launch_pdl(void (*kernel)(Arg), unsigned grid, unsigned block,
+                              cudaStream_t stream, const Arg& arg) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, arg);
+}
+
+// ---------------------------------------------------------------------------
 // Accumulator type per storage type.
 // ---------------------------------------------------------------------------
 template <typename T> struct AccT { using type = float; };
@@ -120,6 +152,24 @@ __device__ __forceinline__ void load4(const __half* p, float v[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// 2 consecutive coefficients -> accumulators (8 B fp32, 4 B bf16/fp16, 16 B fp64).
+__device__ __forceinline__ void load2(const float* p, float v[2]) {
+  float2 a = __ldg(reinterpret_cast<const float2*>(p));
+  v[0] = a.x; v[1] = a.y;
+}
+__device__ __forceinline__ void load2(const double* p, double v[2]) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  v[0] = a.x; v[1] = a.y;
+}
+__device__ __forceinline__ void load2(const __nv_bfloat16* p, float v[2]) {
+  float2 a = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+  v[0] = a.x; v[1] = a.y;
+}
+__device__ __forceinline__ void load2(const __half* p, float v[2]) {
+  float2 a = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+  v[0] = a.x; v[1] = a.y;
+}
+
 // accumulators -> 4 consecutive elements (16 B fp32, 8 B bf16/fp16, 32 B fp64).
 __device__ __forceinline__ void store4(float* p, const float v[4]) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
@@ -142,6 +192,20 @@ __device__ __forceinline__ void store4(__nv_bfloat16* p, const float v[4]) {
 }
 __device__ __forceinline__ void store4(__half* p, const float v[4]) {
   *reinterpret_cast<uint2*>(p) = make_uint2(pack2(p, v[0], v[1]), pack2(p, v[2], v[3]));
+}
+
+// accumulators -> 2 consecutive elements.
+__device__ __forceinline__ void store2(float* p, const float v[2]) {
+  *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+__device__ __forceinline__ void store2(double* p, const double v[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+__device__ __forceinline__ void store2(__nv_bfloat16* p, const float v[2]) {
+  *reinterpret_cast<uint32_t*>(p) = pack2(p, v[0], v[1]);
+}
+__device__ __forceinline__ void store2(__half* p, const float v[2]) {
+  *reinterpret_cast<uint32_t*>(p) = pack2(p, v[0], v[1]);
 }
 
 // accumulators -> 8 consecutive elements.

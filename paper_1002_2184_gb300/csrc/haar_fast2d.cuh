@@ -1,0 +1,381 @@
+// haar_fast2d.cuh -- register/warp-shuffle 2D Fast Haar kernels for images
+// whose sides are multiples of 32 (every workload of interest).
+//
+// Each warp owns a 32 x 32 pixel block; each lane owns a 4-row x 8-column
+// micro-block (lane = 4 * ty + tx, ty = 0..7, tx = 0..3), read or written as
+// four 8-wide row segments with 16-byte accesses.
+//
+// Analysis: levels 1 and 2 run inside the lane's registers (straight from
+// the loads, Fig. 4 applied along rows and then columns); levels 3, 4 and 5
+// pair lanes with warp shuffles (partners lane^4 / lane^1,^8 / lane^2,^16);
+// a sixth level pairs the four warps of a 64 x 64 block through 32 bytes of
+// shared memory.  No other shared memory and no other barrier is used.
+//
+// Synthesis (Eq. 19 along columns, then rows) needs no communication at all:
+// each lane issues all of its loads up front -- its own level-1 and level-2
+// detail coefficients and the (warp-shared, broadcast) coarser ones -- and
+// walks the coarse levels down to its own micro-block.
+//
+// The butterflies perform exactly the same floating-point operations, in
+// the same order, as fwd_quad / inv_quad, so results are bit-identical to
+// the generic kernels.
+#pragma once
+
+#include "haar_kernels.cuh"
+
+namespace fh {
+
+// Mallat band addressing of one image: level-l band coordinates (row, col).
+template <typename T>
+struct Bands {
+  T* base;
+  int64_t rs, h, w;
+  __device__ __forceinline__ T* hx(int l, int64_t row, int64_t col) const {
+    return base + row * rs + (w >> l) + col;
+  }
+  __device__ __forceinline__ T* hy(int l, int64_t row, int64_t col) const {
+    return base + ((h >> l) + row) * rs + col;
+  }
+  __device__ __forceinline__ T* hh(int l, int64_t row, int64_t col) const {
+    return base + ((h >> l) + row) * rs + (w >> l) + col;
+  }
+};
+
+// Horizontal half of a 2x2 butterfly across lanes lane and lane^mask:
+// both lanes get lo = left + right and hi = right - left.
+template <typename A>
+__device__ __forceinline__ void hpair(A v, bool right, int mask, A& lo, A& hi) {
+  const A o = __shfl_xor_sync(0xffffffffu, v, mask);
+  lo = v + o;
+  hi = right ? v - o : o - v;
+}
+
+// Vertical half across lanes lane and lane^mask (top/bottom rows' lo, hi):
+// both lanes get the four bands, as fwd_quad computes them.
+template <typename A>
+__device__ __forceinline__ void vpair(A lo, A hi, bool bottom, int mask, A& ll, A& hx, A& hy,
+                                      A& hh) {
+  const A h = A(0.5);
+  const A olo = __shfl_xor_sync(0xffffffffu, lo, mask);
+  const A ohi = __shfl_xor_sync(0xffffffffu, hi, mask);
+  ll = (lo + olo) * h;
+  hy = (bottom ? lo - olo : olo - lo) * h;
+  hx = (hi + ohi) * h;
+  hh = (bottom ? hi - ohi : ohi - hi) * h;
+}
+
+// One output of the inverse butterfly: the child (qy, qx) of a coarse
+// coefficient, with the same operations as inv_quad.
+template <typename A>
+__device__ __forceinline__ A inv_child(A ll, A hx, A hy, A hh, int qy, int qx) {
+  const A sy = qy ? A(1) : A(-1), sx = qx ? A(1) : A(-1);
+  const A s1 = fma(sy, hy, ll);  // ll -/+ hy, exactly rounded
+  const A s2 = fma(sy, hh, hx);  // hx -/+ hh
+  return fma(sx, s2, s1) * A(0.5);
+}
+
+template <typename Tout, typename A>
+__device__ __forceinline__ void put_ll(const Pass& p, int64_t b, int64_t row, int64_t col, A v) {
+  const int64_t off = b * p.l_bs + row * p.l_rs + col;
+  if (p.ll_acc)
+    static_cast<A*>(p.ll)[off] = v;
+  else
+    st_scalar(static_cast<Tout*>(p.ll) + off, v);
+}
+
+template <typename Tin, typename A>
+__device__ __forceinline__ A get_ll(const Pass& p, int64_t b, int64_t row, int64_t col) {
+  const int64_t off = b * p.l_bs + row * p.l_rs + col;
+  if (p.ll_acc) return static_cast<const A*>(p.ll)[off];
+  return ld_scalar(static_cast<const Tin*>(p.ll) + off);
+}
+
+// ---------------------------------------------------------------------------
+// Analysis.  Block of warps: 1 x 8 (32 x 256 px) for L <= 5, 2 x 4 (64 x 128)
+// for L = 6.
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout, int L>
+__global__ void __launch_bounds__(256) k_dwt2d_fast(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename AccT<Tin>::type;
+  static_assert(L >= 1 && L <= 6, "fast analysis fuses 1..6 levels");
+  constexpr int WR = (L == 6) ? 2 : 1;
+  constexpr int WC = 8 / WR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tx = lane & 3, ty = lane >> 2;
+  const int64_t per = p.tiles_x * p.tiles_y;
+  const int64_t t = blockIdx.x;
+  const int64_t b = t / per, rr = t - b * per;
+  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
+  const int64_t y0 = cy * (32 * WR) + (warp / WC) * 32;
+  const int64_t x0 = cx * (32 * WC) + (warp % WC) * 32;
+  const bool active = (y0 < p.h) && (x0 < p.w);
+  const Bands<Tout> out{static_cast<Tout*>(p.dst) + b * p.d_bs, p.d_rs, p.h, p.w};
+  const int64_t py = y0 + 4 * ty, px = x0 + 8 * tx;
+  A l5 = A(0);
+
+  if (active) {
+    const Tin* src = static_cast<const Tin*>(p.src) + b * p.s_bs + py * p.s_rs + px;
+    A v[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) load8(src + r * p.s_rs, v[r]);
+
+    // ---- level 1: eight 2x2 blocks per lane ----
+    A l1[2][4];
+#pragma unroll
+    for (int rp = 0; rp < 2; ++rp) {
+      A hx[4], hy[4], hh[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        fwd_quad(v[2 * rp][2 * c], v[2 * rp][2 * c + 1], v[2 * rp + 1][2 * c],
+                 v[2 * rp + 1][2 * c + 1], l1[rp][c], hx[c], hy[c], hh[c]);
+      const int64_t row = (py >> 1) + rp, col = px >> 1;
+      store4(out.hx(1, row, col), hx);
+      store4(out.hy(1, row, col), hy);
+      store4(out.hh(1, row, col), hh);
+    }
+    if constexpr (L == 1) {
+#pragma unroll
+      for (int rp = 0; rp < 2; ++rp) {
+        const int64_t row = (py >> 1) + rp, col = px >> 1;
+        if (!p.ll_acc) {
+          store4(static_cast<Tout*>(p.ll) + b * p.l_bs + row * p.l_rs + col, l1[rp]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) put_ll<Tout>(p, b, row, col + c, l1[rp][c]);
+        }
+      }
+    } else {
+      // ---- level 2: two 2x2 blocks of LL1 per lane ----
+      A l2[2];
+      {
+        A hx[2], hy[2], hh[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          fwd_quad(l1[0][2 * c], l1[0][2 * c + 1], l1[1][2 * c], l1[1][2 * c + 1], l2[c], hx[c],
+                   hy[c], hh[c]);
+        const int64_t row = py >> 2, col = px >> 2;
+        store2(out.hx(2, row, col), hx);
+        store2(out.hy(2, row, col), hy);
+        store2(out.hh(2, row, col), hh);
+      }
+      if constexpr (L == 2) {
+        const int64_t row = py >> 2, col = px >> 2;
+        if (!p.ll_acc) {
+          store2(static_cast<Tout*>(p.ll) + b * p.l_bs + row * p.l_rs + col, l2);
+        } else {
+          put_ll<Tout>(p, b, row, col, l2[0]);
+          put_ll<Tout>(p, b, row, col + 1, l2[1]);
+        }
+      } else {
+        // ---- level 3: horizontal pair in the lane, vertical pair lane^4 ----
+        A l3, x3, y3, z3;
+        vpair(l2[0] + l2[1], l2[1] - l2[0], (ty & 1) != 0, 4, l3, x3, y3, z3);
+        const int64_t r3 = py >> 3, c3 = px >> 3;
+        const bool own3 = (ty & 1) == 0;
+        if (own3) {
+          st_scalar(out.hx(3, r3, c3), x3);
+          st_scalar(out.hy(3, r3, c3), y3);
+          st_scalar(out.hh(3, r3, c3), z3);
+        }
+        if constexpr (L == 3) {
+          if (own3) put_ll<Tout>(p, b, r3, c3, l3);
+        } else {
+          // ---- level 4: pairs lane^1 (columns) and lane^8 (rows) ----
+          A lo, hi, l4, x4, y4, z4;
+          hpair(l3, (tx & 1) != 0, 1, lo, hi);
+          vpair(lo, hi, ((ty >> 1) & 1) != 0, 8, l4, x4, y4, z4);
+          const int64_t r4 = py >> 4, c4 = px >> 4;
+          const bool own4 = (ty & 3) == 0 && (tx & 1) == 0;
+          if (own4) {
+            st_scalar(out.hx(4, r4, c4), x4);
+            st_scalar(out.hy(4, r4, c4), y4);
+            st_scalar(out.hh(4, r4, c4), z4);
+          }
+          if constexpr (L == 4) {
+            if (own4) put_ll<Tout>(p, b, r4, c4, l4);
+          } else {
+            // ---- level 5: pairs lane^2 (columns) and lane^16 (rows) ----
+            A lo5, hi5, x5, y5, z5;
+            hpair(l4, (tx & 2) != 0, 2, lo5, hi5);
+            vpair(lo5, hi5, (ty & 4) != 0, 16, l5, x5, y5, z5);
+            if (lane == 0) {
+              const int64_t r5 = py >> 5, c5 = px >> 5;
+              st_scalar(out.hx(5, r5, c5), x5);
+              st_scalar(out.hy(5, r5, c5), y5);
+              st_scalar(out.hh(5, r5, c5), z5);
+              if constexpr (L == 5) put_ll<Tout>(p, b, r5, c5, l5);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  if constexpr (L == 6) {
+    // ---- level 6: the four warps of each 64 x 64 block ----
+    __shared__ A s5[WR][WC];
+    if (lane == 0) s5[warp / WC][warp % WC] = l5;
+    __syncthreads();
+    if (threadIdx.x < WC / 2) {
+      const int j = threadIdx.x;
+      const int64_t by0 = cy * 64, bx0 = cx * 128 + 64 * j;
+      if (by0 < p.h && bx0 < p.w) {
+        A l6, x6, y6, z6;
+        fwd_quad(s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j], s5[1][2 * j + 1], l6, x6, y6, z6);
+        const int64_t r6 = by0 >> 6, c6 = bx0 >> 6;
+        st_scalar(out.hx(6, r6, c6), x6);
+        st_scalar(out.hy(6, r6, c6), y6);
+        st_scalar(out.hh(6, r6, c6), z6);
+        put_ll<Tout>(p, b, r6, c6, l6);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Synthesis.  Block of warps: 1 x 8 (32 x 256 px) for every L.
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout, int L>
+__global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename AccT<Tin>::type;
+  static_assert(L >= 1 && L <= 6, "fast synthesis fuses 1..6 levels");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tx = lane & 3, ty = lane >> 2;
+  const int64_t per = p.tiles_x * p.tiles_y;
+  const int64_t t = blockIdx.x;
+  const int64_t b = t / per, rr = t - b * per;
+  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
+  const int64_t y0 = cy * 32, x0 = cx * 256 + warp * 32;
+  if (y0 >= p.h || x0 >= p.w) return;
+  const Bands<const Tin> in{static_cast<const Tin*>(p.src) + b * p.s_bs, p.s_rs, p.h, p.w};
+  const int64_t py = y0 + 4 * ty, px = x0 + 8 * tx;
+
+  // ---- every load first ----
+  A d1x[2][4], d1y[2][4], d1z[2][4];
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp) {
+    const int64_t row = (py >> 1) + rp, col = px >> 1;
+    load4(in.hx(1, row, col), d1x[rp]);
+    load4(in.hy(1, row, col), d1y[rp]);
+    load4(in.hh(1, row, col), d1z[rp]);
+  }
+  A ll1[2][4];
+  A ll2[2];
+  A d2x[2], d2y[2], d2z[2];
+  A cxv[7], cyv[7], czv[7];  // levels 3..L
+  A llL = A(0);
+  if constexpr (L == 1) {
+#pragma unroll
+    for (int rp = 0; rp < 2; ++rp) {
+      const int64_t row = (py >> 1) + rp, col = px >> 1;
+      if (!p.ll_acc) {
+        load4(static_cast<const Tin*>(p.ll) + b * p.l_bs + row * p.l_rs + col, ll1[rp]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ll1[rp][c] = get_ll<Tin, A>(p, b, row, col + c);
+      }
+    }
+  } else {
+    const int64_t row = py >> 2, col = px >> 2;
+    load2(in.hx(2, row, col), d2x);
+    load2(in.hy(2, row, col), d2y);
+    load2(in.hh(2, row, col), d2z);
+    if constexpr (L == 2) {
+      if (!p.ll_acc) {
+        load2(static_cast<const Tin*>(p.ll) + b * p.l_bs + row * p.l_rs + col, ll2);
+      } else {
+        ll2[0] = get_ll<Tin, A>(p, b, row, col);
+        ll2[1] = get_ll<Tin, A>(p, b, row, col + 1);
+      }
+    } else {
+#pragma unroll
+      for (int l = 3; l <= L; ++l) {
+        const int64_t r = py >> l, c = px >> l;
+        cxv[l] = ld_scalar(in.hx(l, r, c));
+        cyv[l] = ld_scalar(in.hy(l, r, c));
+        czv[l] = ld_scalar(in.hh(l, r, c));
+      }
+      llL = get_ll<Tin, A>(p, b, py >> L, px >> L);
+    }
+  }
+
+  // ---- coarse levels: walk down to this lane's LL2 pair ----
+  if constexpr (L >= 3) {
+    A v = llL;
+#pragma unroll
+    for (int l = L; l >= 4; --l)
+      v = inv_child(v, cxv[l], cyv[l], czv[l], (int)((py >> (l - 1)) & 1),
+                    (int)((px >> (l - 1)) & 1));
+    const int qy = (int)((py >> 2) & 1);
+    ll2[0] = inv_child(v, cxv[3], cyv[3], czv[3], qy, 0);
+    ll2[1] = inv_child(v, cxv[3], cyv[3], czv[3], qy, 1);
+  }
+  // ---- level 2: LL1 (2 x 4) ----
+  if constexpr (L >= 2) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      inv_quad(ll2[c], d2x[c], d2y[c], d2z[c], ll1[0][2 * c], ll1[0][2 * c + 1], ll1[1][2 * c],
+               ll1[1][2 * c + 1]);
+  }
+  // ---- level 1: the 4 x 8 micro-block ----
+  Tout* dst = static_cast<Tout*>(p.dst) + b * p.d_bs + py * p.d_rs + px;
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp) {
+    A o0[8], o1[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      inv_quad(ll1[rp][c], d1x[rp][c], d1y[rp][c], d1z[rp][c], o0[2 * c], o0[2 * c + 1],
+               o1[2 * c], o1[2 * c + 1]);
+    store8(dst + (2 * rp) * p.d_rs, o0);
+    store8(dst + (2 * rp + 1) * p.d_rs, o1);
+  }
+}
+
+template <typename Tin, typename Tout>
+cudaError_t dwt2d_fast_t(Pass p, cudaStream_t s) {
+  const int CH = p.levels == 6 ? 64 : 32, CW = p.levels == 6 ? 128 : 256;
+  p.tiles_x = (p.w + CW - 1) / CW;
+  p.tiles_y = (p.h + CH - 1) / CH;
+  p.ntiles = p.batch * p.tiles_x * p.tiles_y;
+  if (p.ntiles == 0) return cudaSuccess;
+  if (p.ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned g = (unsigned)p.ntiles;
+  cudaError_t e = cudaSuccess;
+  switch (p.levels) {
+    case 1: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 1>, g, 256, s, p); break;
+    case 2: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 2>, g, 256, s, p); break;
+    case 3: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 3>, g, 256, s, p); break;
+    case 4: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 4>, g, 256, s, p); break;
+    case 5: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 5>, g, 256, s, p); break;
+    case 6: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 6>, g, 256, s, p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return e;
+}
+
+template <typename Tin, typename Tout>
+cudaError_t idwt2d_fast_t(Pass p, cudaStream_t s) {
+  p.tiles_x = (p.w + 255) / 256;
+  p.tiles_y = (p.h + 31) / 32;
+  p.ntiles = p.batch * p.tiles_x * p.tiles_y;
+  if (p.ntiles == 0) return cudaSuccess;
+  if (p.ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned g = (unsigned)p.ntiles;
+  cudaError_t e = cudaSuccess;
+  switch (p.levels) {
+    case 1: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 1>, g, 256, s, p); break;
+    case 2: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 2>, g, 256, s, p); break;
+    case 3: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 3>, g, 256, s, p); break;
+    case 4: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 4>, g, 256, s, p); break;
+    case 5: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 5>, g, 256, s, p); break;
+    case 6: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 6>, g, 256, s, p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return e;
+}
+
+}  // namespace fh

@@ -44,9 +44,11 @@ struct Pass {
   int64_t tiles_x, tiles_y, ntiles;
 };
 
-// Tile shapes of the 2D kernels (vector path).  The scalar path always uses
-// a 64 x 64 tile.
-enum Tile2Cfg { kT32x128 = 0, kT64x128 = 1, kT64x64 = 2, kTileCount = 3 };
+// Tile shapes of the generic 2D kernels (vector path); the scalar path always
+// uses a 64 x 64 tile.  kFast selects the register/warp-shuffle kernels
+// (haar_fast2d.cuh), valid when both sides are multiples of 32, the rows are
+// vector aligned and the pass fuses at most 6 levels.
+enum Tile2Cfg { kT32x128 = 0, kT64x128 = 1, kT64x64 = 2, kFast = 3, kTileCount = 4 };
 inline int tile_h(int cfg) { return cfg == kT32x128 ? 32 : 64; }
 inline int tile_w(int cfg) { return cfg == kT64x64 ? 64 : 128; }
 inline int tile_max_levels(int cfg) { return cfg == kT32x128 ? 5 : 6; }

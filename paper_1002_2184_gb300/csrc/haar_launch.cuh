@@ -3,6 +3,7 @@
 #pragma once
 
 #include "haar_internal.h"
+#include "haar_fast2d.cuh"
 #include "haar_kernels.cuh"
 
 namespace fh {
@@ -60,6 +61,8 @@ __device__ __forceinline__ Tile2 make_tile2_inv(const Pass& p, int64_t tile, int
 
 template <typename Tin, typename Tout, int TH, int TW, bool VEC>
 __global__ void __launch_bounds__(kNT2) k_dwt2d(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename AccT<Tin>::type;
   __shared__ __align__(16) A S[TH / 2][TW / 2 + kPad];
   for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
@@ -71,6 +74,8 @@ __global__ void __launch_bounds__(kNT2) k_dwt2d(const Pass p) {
 
 template <typename Tin, typename Tout, int TH, int TW, bool VEC>
 __global__ void __launch_bounds__(kNT2) k_idwt2d(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename AccT<Tin>::type;
   __shared__ __align__(16) A S[TH / 2][TW / 2 + kPad];
   for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
@@ -91,40 +96,44 @@ inline unsigned grid_for(int64_t ntiles, int grid_cap) {
 
 template <typename Tin, typename Tout>
 cudaError_t dwt2d_t(Pass p, int cfg, bool vec, int grid_cap, cudaStream_t s) {
+  if (cfg == kFast) return dwt2d_fast_t<Tin, Tout>(p, s);
   const int TH = vec ? tile_h(cfg) : 64, TW = vec ? tile_w(cfg) : 64;
   p.tiles_x = ceil_div(p.w, TW);
   p.tiles_y = ceil_div(p.h, TH);
   p.ntiles = p.batch * p.tiles_x * p.tiles_y;
   if (p.ntiles == 0) return cudaSuccess;
   const unsigned g = grid_for(p.ntiles, grid_cap);
+  cudaError_t e = cudaSuccess;
   if (!vec)
-    k_dwt2d<Tin, Tout, 64, 64, false><<<g, kNT2, 0, s>>>(p);
+    e = launch_pdl(k_dwt2d<Tin, Tout, 64, 64, false>, g, kNT2, s, p);
   else if (cfg == kT32x128)
-    k_dwt2d<Tin, Tout, 32, 128, true><<<g, kNT2, 0, s>>>(p);
+    e = launch_pdl(k_dwt2d<Tin, Tout, 32, 128, true>, g, kNT2, s, p);
   else if (cfg == kT64x128)
-    k_dwt2d<Tin, Tout, 64, 128, true><<<g, kNT2, 0, s>>>(p);
+    e = launch_pdl(k_dwt2d<Tin, Tout, 64, 128, true>, g, kNT2, s, p);
   else
-    k_dwt2d<Tin, Tout, 64, 64, true><<<g, kNT2, 0, s>>>(p);
-  return cudaGetLastError();
+    e = launch_pdl(k_dwt2d<Tin, Tout, 64, 64, true>, g, kNT2, s, p);
+  return e;
 }
 
 template <typename Tin, typename Tout>
 cudaError_t idwt2d_t(Pass p, int cfg, bool vec, int grid_cap, cudaStream_t s) {
+  if (cfg == kFast) return idwt2d_fast_t<Tin, Tout>(p, s);
   const int TH = vec ? tile_h(cfg) : 64, TW = vec ? tile_w(cfg) : 64;
   p.tiles_x = ceil_div(p.w, TW);
   p.tiles_y = ceil_div(p.h, TH);
   p.ntiles = p.batch * p.tiles_x * p.tiles_y;
   if (p.ntiles == 0) return cudaSuccess;
   const unsigned g = grid_for(p.ntiles, grid_cap);
+  cudaError_t e = cudaSuccess;
   if (!vec)
-    k_idwt2d<Tin, Tout, 64, 64, false><<<g, kNT2, 0, s>>>(p);
+    e = launch_pdl(k_idwt2d<Tin, Tout, 64, 64, false>, g, kNT2, s, p);
   else if (cfg == kT32x128)
-    k_idwt2d<Tin, Tout, 32, 128, true><<<g, kNT2, 0, s>>>(p);
+    e = launch_pdl(k_idwt2d<Tin, Tout, 32, 128, true>, g, kNT2, s, p);
   else if (cfg == kT64x128)
-    k_idwt2d<Tin, Tout, 64, 128, true><<<g, kNT2, 0, s>>>(p);
+    e = launch_pdl(k_idwt2d<Tin, Tout, 64, 128, true>, g, kNT2, s, p);
   else
-    k_idwt2d<Tin, Tout, 64, 64, true><<<g, kNT2, 0, s>>>(p);
-  return cudaGetLastError();
+    e = launch_pdl(k_idwt2d<Tin, Tout, 64, 64, true>, g, kNT2, s, p);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -133,6 +142,8 @@ cudaError_t idwt2d_t(Pass p, int cfg, bool vec, int grid_cap, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout, int CH, int NT, bool VEC>
 __global__ void __launch_bounds__(NT) k_dwt1d(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename AccT<Tin>::type;
   __shared__ __align__(16) A S[CH / 2];
   for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
@@ -153,6 +164,8 @@ __global__ void __launch_bounds__(NT) k_dwt1d(const Pass p) {
 
 template <typename Tin, typename Tout, int CH, int NT, bool VEC>
 __global__ void __launch_bounds__(NT) k_idwt1d(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename AccT<Tin>::type;
   __shared__ __align__(16) A S[CH / 2];
   for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
@@ -179,18 +192,19 @@ cudaError_t dwt1d_t(Pass p, int cfg, bool vec, cudaStream_t s) {
   p.ntiles = p.batch * p.h * p.tiles_x;
   if (p.ntiles == 0) return cudaSuccess;
   const unsigned g = grid_for(p.ntiles, 0);
+  cudaError_t e = cudaSuccess;
   if (cfg == kC1024) {
     if (vec)
-      k_dwt1d<Tin, Tout, 1024, 128, true><<<g, 128, 0, s>>>(p);
+      e = launch_pdl(k_dwt1d<Tin, Tout, 1024, 128, true>, g, 128, s, p);
     else
-      k_dwt1d<Tin, Tout, 1024, 128, false><<<g, 128, 0, s>>>(p);
+      e = launch_pdl(k_dwt1d<Tin, Tout, 1024, 128, false>, g, 128, s, p);
   } else {
     if (vec)
-      k_dwt1d<Tin, Tout, 4096, 256, true><<<g, 256, 0, s>>>(p);
+      e = launch_pdl(k_dwt1d<Tin, Tout, 4096, 256, true>, g, 256, s, p);
     else
-      k_dwt1d<Tin, Tout, 4096, 256, false><<<g, 256, 0, s>>>(p);
+      e = launch_pdl(k_dwt1d<Tin, Tout, 4096, 256, false>, g, 256, s, p);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 template <typename Tin, typename Tout>
@@ -201,18 +215,19 @@ cudaError_t idwt1d_t(Pass p, int cfg, bool vec, cudaStream_t s) {
   p.ntiles = p.batch * p.h * p.tiles_x;
   if (p.ntiles == 0) return cudaSuccess;
   const unsigned g = grid_for(p.ntiles, 0);
+  cudaError_t e = cudaSuccess;
   if (cfg == kC1024) {
     if (vec)
-      k_idwt1d<Tin, Tout, 1024, 128, true><<<g, 128, 0, s>>>(p);
+      e = launch_pdl(k_idwt1d<Tin, Tout, 1024, 128, true>, g, 128, s, p);
     else
-      k_idwt1d<Tin, Tout, 1024, 128, false><<<g, 128, 0, s>>>(p);
+      e = launch_pdl(k_idwt1d<Tin, Tout, 1024, 128, false>, g, 128, s, p);
   } else {
     if (vec)
-      k_idwt1d<Tin, Tout, 4096, 256, true><<<g, 256, 0, s>>>(p);
+      e = launch_pdl(k_idwt1d<Tin, Tout, 4096, 256, true>, g, 256, s, p);
     else
-      k_idwt1d<Tin, Tout, 4096, 256, false><<<g, 256, 0, s>>>(p);
+      e = launch_pdl(k_idwt1d<Tin, Tout, 4096, 256, false>, g, 256, s, p);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 // Dispatch on the output type for one input type.

@@ -54,17 +54,25 @@ def images(batch, h, w, seed=0):
 # ---------------------------------------------------------------------------
 # 2D
 # ---------------------------------------------------------------------------
+# Sides that are multiples of 32 run the register/shuffle kernels (one per
+# level count 1..6); other sides divisible by 8 run the shared-memory tile
+# kernels; the rest (or misaligned rows) run the scalar tile kernels.
 CASES_2D = [
-    (1, 2, 2, 1),        # smallest image
-    (1, 8, 8, 3),        # full depth of a tiny image
-    (2, 64, 64, 6),      # one 64x128 tile, partly filled
-    (1, 96, 160, 5),     # ragged tail in both directions
-    (3, 32, 256, 5),     # several tiles per row, batch of 3
-    (1, 128, 64, 6),     # tall image
-    (1, 256, 512, 8),    # two chained passes (6 + 2 levels)
+    (1, 2, 2, 1),        # smallest image (scalar)
+    (1, 8, 8, 3),        # full depth of a tiny image (tile kernel)
+    (2, 64, 64, 6),      # fast, six levels, CTA half outside the image
+    (1, 96, 160, 5),     # fast, partial CTA in both directions
+    (3, 32, 256, 5),     # fast, batch of 3
+    (1, 128, 64, 6),     # fast, tall image
+    (1, 256, 512, 8),    # two chained passes (6 fast + 2 on a 4 x 8 image)
     (1, 1024, 1024, 10),
-    (2, 192, 320, 1),    # one level
-    (1, 48, 40, 3),      # w % 8 != 0 -> scalar path
+    (2, 192, 320, 1),    # fast, one level
+    (1, 64, 96, 2),      # fast, two levels
+    (2, 128, 96, 3),     # fast, three levels
+    (1, 96, 64, 4),      # fast, four levels
+    (1, 48, 40, 3),      # sides not multiples of 32 -> tile kernel
+    (1, 80, 120, 3),     # tile kernel, ragged tiles
+    (1, 48, 36, 2),      # w % 8 != 0 -> scalar kernel
 ]
 
 
@@ -182,7 +190,8 @@ CASES_1D = [
     (1, 4, 1024, 10),
     (1, 1, 4096 + 8, 3),
     (1, 2, 1 << 20, 16),     # two chained passes (12 + 4)
-    (1, 1, 1000, 3),         # n % 8 != 0 -> scalar path
+    (1, 1, 1000, 3),         # ragged chunk tail
+    (1, 3, 1004, 2),         # n % 8 != 0 -> scalar path
 ]
 
 
@@ -226,3 +235,27 @@ def test_empty_tensors():
     x = torch.empty((0, 64, 64), device=DEV)
     assert api.dwt2d(x, 3).shape == (0, 64, 64)
     assert api.idwt1d(torch.empty((3, 0), device=DEV), 2).shape == (3, 0)
+
+
+def test_plan_and_graph_capture_match_eager():
+    """A Plan replayed from a CUDA graph gives the same coefficients and
+    reconstruction as the one-shot calls, including a deep (chained,
+    workspace-using) transform."""
+    for levels in (5, 8):
+        x = dev(images(2, 256, 512, seed=levels), torch.float32)
+        c = torch.empty_like(x)
+        y = torch.empty_like(x)
+        plan = api.Plan(x, c, levels, y)
+        plan.dwt()
+        plan.idwt()
+        torch.cuda.synchronize()
+        c.zero_()
+        y.zero_()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.dwt()
+            plan.idwt()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(c, api.dwt2d(x, levels))
+        assert torch.equal(y, api.idwt2d(api.dwt2d(x, levels), levels))
