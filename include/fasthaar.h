@@ -62,7 +62,8 @@ enum {
   HAAR_EALIAS = -4,     /* input and output memory ranges overlap */
   HAAR_ECUDA = -5,      /* a CUDA runtime call failed; see haar_last_cuda_error() */
   HAAR_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
-  HAAR_EWORKSPACE = -7  /* workspace missing or smaller than haar_workspace_size() */
+  HAAR_EWORKSPACE = -7, /* workspace missing or smaller than haar_workspace_size() */
+  HAAR_EQUEUE = -8      /* a persistent launch found its work queue inconsistent */
 };
 
 /* Storage types.  uint8 is accepted as analysis input only (values 0..255
@@ -127,6 +128,72 @@ int haar_dwt_2d(const haar_desc *x, const haar_desc *coef, int levels, void *wor
  * dtypes as haar_idwt_1d. */
 int haar_idwt_2d(const haar_desc *coef, const haar_desc *x, int levels, void *workspace,
                  size_t workspace_bytes, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Ragged batches: many 2D images of different sizes and level counts in one
+ * persistent launch.  Images live anywhere inside one input buffer and one
+ * output buffer (element offsets from the two base pointers); the output of
+ * each image is its Mallat layout (analysis) or the image (synthesis).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int64_t in_offset;      /* elements from the input base pointer to pixel (0, 0) */
+  int64_t out_offset;     /* elements from the output base pointer */
+  int64_t h, w;           /* multiples of 32, divisible by 2^levels */
+  int64_t in_row_stride;  /* elements; >= w */
+  int64_t out_row_stride; /* elements; >= w */
+  int32_t levels;         /* 1..6 */
+  int32_t reserved;       /* must be 0 */
+} haar_ragged_item;
+
+/* Work-unit shape of the persistent kernel: 64 x 128 pixels (any level count)
+ * or 32 x 256 pixels (every image at most 5 levels). */
+enum { HAAR_UNIT_64x128 = 0, HAAR_UNIT_32x256 = 1 };
+
+typedef struct haar_ragged_plan haar_ragged_plan; /* opaque, host memory */
+
+/* Builds a plan (host only, no device call): validates every item, cuts each
+ * image into work units and prepares the device image table.
+ * blocks_per_sm: blocks per SM of the persistent grid (1..32); the grid is
+ * min(units, blocks_per_sm * SM count of the device current at launch).
+ * Errors: HAAR_EINVAL (bad item or argument), HAAR_ESHAPE (side not a
+ * multiple of 32 or not divisible by 2^levels, or 6 levels with the
+ * 32 x 256 unit).  On success *plan must be released with
+ * haar_ragged_plan_destroy. */
+int haar_ragged_plan_create(const haar_ragged_item *items, int64_t count, int unit,
+                            int blocks_per_sm, haar_ragged_plan **plan);
+
+/* Device workspace the plan needs (header + image table), in bytes. */
+int haar_ragged_workspace_size(const haar_ragged_plan *plan, size_t *bytes);
+
+/* Work units, pixels and the persistent grid size of a plan on the current
+ * device (queries its SM count). */
+int haar_ragged_plan_info(const haar_ragged_plan *plan, int64_t *units, int64_t *pixels,
+                          int64_t *grid);
+
+/* Copies the image table into the workspace and zeroes its counters
+ * (asynchronous on the stream; the plan must outlive the copy).  Call once
+ * per workspace, before the first transform (and before any graph capture). */
+int haar_ragged_upload(const haar_ragged_plan *plan, void *workspace, size_t workspace_bytes,
+                       void *cuda_stream);
+
+/* One persistent launch transforming every image of the plan.  dtypes as
+ * haar_dwt_2d / haar_idwt_2d.  The workspace must have been uploaded; the
+ * kernel leaves its counters zeroed again, so the call can be repeated or
+ * replayed from a CUDA graph.  Two calls on one workspace must not overlap in
+ * time (same stream, or ordered by events). */
+int haar_dwt_2d_ragged(const haar_ragged_plan *plan, const void *in, int in_dtype, void *out,
+                       int out_dtype, void *workspace, size_t workspace_bytes, void *cuda_stream);
+int haar_idwt_2d_ragged(const haar_ragged_plan *plan, const void *in, int in_dtype, void *out,
+                        int out_dtype, void *workspace, size_t workspace_bytes,
+                        void *cuda_stream);
+
+/* Reads (synchronously: it waits for the stream) the workspace's error word:
+ * *status = HAAR_OK, or HAAR_EQUEUE if a launch found its work queue in an
+ * inconsistent state (the word is then cleared). */
+int haar_ragged_status(const haar_ragged_plan *plan, void *workspace, int *status,
+                       void *cuda_stream);
+
+int haar_ragged_plan_destroy(haar_ragged_plan *plan);
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *haar_status_string(int status);

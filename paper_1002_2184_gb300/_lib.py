@@ -21,9 +21,13 @@ HAAR_EALIAS = -4
 HAAR_ECUDA = -5
 HAAR_ETIMEOUT = -6
 HAAR_EWORKSPACE = -7
+HAAR_EQUEUE = -8
 
 # Storage types.
 HAAR_F32, HAAR_BF16, HAAR_F16, HAAR_U8, HAAR_F64 = 0, 1, 2, 3, 4
+
+# Ragged work-unit shapes.
+HAAR_UNIT_64x128, HAAR_UNIT_32x256 = 0, 1
 
 # Workspace-size operation codes.
 HAAR_OP_DWT_1D, HAAR_OP_IDWT_1D, HAAR_OP_DWT_2D, HAAR_OP_IDWT_2D = 0, 1, 2, 3
@@ -39,6 +43,19 @@ class HaarDesc(ctypes.Structure):
         ("w", ctypes.c_int64),
         ("batch_stride", ctypes.c_int64),
         ("row_stride", ctypes.c_int64),
+    ]
+
+
+class HaarRaggedItem(ctypes.Structure):
+    _fields_ = [
+        ("in_offset", ctypes.c_int64),
+        ("out_offset", ctypes.c_int64),
+        ("h", ctypes.c_int64),
+        ("w", ctypes.c_int64),
+        ("in_row_stride", ctypes.c_int64),
+        ("out_row_stride", ctypes.c_int64),
+        ("levels", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -68,6 +85,20 @@ SIGNATURES = {
     "haar_idwt_1d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_dwt_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_idwt_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "haar_ragged_plan_create": (ctypes.c_int, [ctypes.POINTER(HaarRaggedItem), ctypes.c_int64,
+                                               ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_void_p)]),
+    "haar_ragged_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "haar_ragged_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "haar_ragged_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "haar_dwt_2d_ragged": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P,
+                                          ctypes.c_size_t, _P]),
+    "haar_idwt_2d_ragged": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P,
+                                           ctypes.c_size_t, _P]),
+    "haar_ragged_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), _P]),
+    "haar_ragged_plan_destroy": (ctypes.c_int, [_P]),
 }
 
 

@@ -188,3 +188,94 @@ class Plan:
                        self._stream(stream))
         if rc:
             _lib.check(rc, "idwt")
+
+
+class RaggedPlan:
+    """A ragged batch of 2D images (different sizes and level counts) packed
+    one after another in flat buffers, transformed by one persistent launch.
+
+    ``items`` is a list of (h, w, levels); image i occupies elements
+    ``offsets[i] : offsets[i] + h*w`` (row-major, contiguous) of every flat
+    buffer used with this plan.  ``unit`` and ``blocks_per_sm`` select the
+    work-unit shape and the persistent grid (see autotune.tune_ragged).
+    The workspace is allocated and uploaded once; dwt()/idwt() are then
+    single launches, safe to capture into a CUDA graph.
+    """
+
+    def __init__(self, items, device, unit: int = _lib.HAAR_UNIT_64x128,
+                 blocks_per_sm: int = 4):
+        self.lib = _lib.load()
+        self.items = [(int(h), int(w), int(L)) for h, w, L in items]
+        self.device = torch.device(device)
+        self.unit, self.blocks_per_sm = int(unit), int(blocks_per_sm)
+        offs, o = [], 0
+        for h, w, _ in self.items:
+            offs.append(o)
+            o += h * w
+        self.offsets, self.numel = offs, o
+        arr = (_lib.HaarRaggedItem * max(1, len(self.items)))()
+        for i, ((h, w, L), off) in enumerate(zip(self.items, offs)):
+            arr[i] = _lib.HaarRaggedItem(off, off, h, w, w, w, L, 0)
+        handle = ctypes.c_void_p()
+        _lib.check(self.lib.haar_ragged_plan_create(arr, len(self.items), self.unit,
+                                                    self.blocks_per_sm, ctypes.byref(handle)),
+                   "haar_ragged_plan_create")
+        self._h = handle
+        n = ctypes.c_size_t()
+        _lib.check(self.lib.haar_ragged_workspace_size(handle, ctypes.byref(n)),
+                   "haar_ragged_workspace_size")
+        self._ws_n = n.value
+        self._ws = torch.empty(self._ws_n, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.haar_ragged_upload(handle, self._ws.data_ptr(), self._ws_n,
+                                                   torch.cuda.current_stream(self.device)
+                                                   .cuda_stream), "haar_ragged_upload")
+
+    def info(self):
+        u, p, g = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.haar_ragged_plan_info(self._h, ctypes.byref(u), ctypes.byref(p),
+                                                      ctypes.byref(g)), "haar_ragged_plan_info")
+        return {"units": u.value, "pixels": p.value, "grid": g.value}
+
+    def empty(self, dtype=torch.float32) -> torch.Tensor:
+        return torch.empty(self.numel, dtype=dtype, device=self.device)
+
+    def views(self, flat: torch.Tensor):
+        """The (h, w) image views of a flat buffer laid out by this plan."""
+        return [flat[o:o + h * w].view(h, w) for (h, w, _), o in zip(self.items, self.offsets)]
+
+    def _run(self, fn, src: torch.Tensor, dst: torch.Tensor, stream=None):
+        if src.numel() < self.numel or dst.numel() < self.numel:
+            raise ValueError("buffer smaller than the plan's layout")
+        if not (src.is_contiguous() and dst.is_contiguous()):
+            raise ValueError("ragged buffers must be contiguous")
+        st = (torch.cuda.current_stream(self.device).cuda_stream if stream is None
+              else getattr(stream, "cuda_stream", stream))
+        rc = fn(self._h, src.data_ptr(), haar_dtype(src.dtype), dst.data_ptr(),
+                haar_dtype(dst.dtype), self._ws.data_ptr(), self._ws_n, st)
+        if rc:
+            _lib.check(rc, "ragged transform")
+        return dst
+
+    def dwt(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        return self._run(self.lib.haar_dwt_2d_ragged, x, out, stream)
+
+    def idwt(self, c: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        return self._run(self.lib.haar_idwt_2d_ragged, c, out, stream)
+
+    def status(self) -> int:
+        """HAAR_OK, or HAAR_EQUEUE if a launch saw an inconsistent queue
+        (synchronises the current stream)."""
+        st = ctypes.c_int(0)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.haar_ragged_status(self._h, self._ws.data_ptr(), ctypes.byref(st),
+                                                   torch.cuda.current_stream(self.device)
+                                                   .cuda_stream), "haar_ragged_status")
+        return st.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._LIB is not None:
+            _lib._LIB.haar_ragged_plan_destroy(h)
+            self._h = None

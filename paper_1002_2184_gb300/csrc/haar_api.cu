@@ -17,6 +17,12 @@ int cuda_fail(cudaError_t e) {
   return HAAR_ECUDA;
 }
 
+}  // namespace
+
+void fh::set_last_cuda_error(int e) { g_last_cuda = e; }
+
+namespace {
+
 bool dtype_known(int dt) { return dt >= HAAR_F32 && dt <= HAAR_F64; }
 
 int acc_dtype(int dt) { return dt == HAAR_F64 ? HAAR_F64 : HAAR_F32; }
@@ -223,6 +229,7 @@ const char* haar_status_string(int status) {
     case HAAR_ECUDA: return "CUDA error";
     case HAAR_ETIMEOUT: return "device wait timed out";
     case HAAR_EWORKSPACE: return "workspace missing or too small";
+    case HAAR_EQUEUE: return "work queue inconsistent";
   }
   return "unknown status";
 }

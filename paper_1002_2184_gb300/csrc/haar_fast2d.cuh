@@ -21,6 +21,7 @@
 // the generic kernels.
 #pragma once
 
+#include "haar_internal.h"
 #include "haar_kernels.cuh"
 
 namespace fh {
@@ -74,187 +75,172 @@ __device__ __forceinline__ A inv_child(A ll, A hx, A hy, A hh, int qy, int qx) {
   return fma(sx, s2, s1) * A(0.5);
 }
 
+// One image of a pass (pointers already offset to the batch item).
+struct Img2 {
+  const void* src;
+  int64_t s_rs;
+  void* dst;
+  int64_t d_rs;
+  void* ll;  // LL destination (analysis) or source (synthesis)
+  int64_t l_rs;
+  int ll_acc;  // 1: ll is accumulator typed (workspace), 0: coefficient typed
+  int64_t h, w;
+};
+
 template <typename Tout, typename A>
-__device__ __forceinline__ void put_ll(const Pass& p, int64_t b, int64_t row, int64_t col, A v) {
-  const int64_t off = b * p.l_bs + row * p.l_rs + col;
-  if (p.ll_acc)
-    static_cast<A*>(p.ll)[off] = v;
+__device__ __forceinline__ void put_ll(const Img2& im, int64_t row, int64_t col, A v) {
+  const int64_t off = row * im.l_rs + col;
+  if (im.ll_acc)
+    static_cast<A*>(im.ll)[off] = v;
   else
-    st_scalar(static_cast<Tout*>(p.ll) + off, v);
+    st_scalar(static_cast<Tout*>(im.ll) + off, v);
 }
 
 template <typename Tin, typename A>
-__device__ __forceinline__ A get_ll(const Pass& p, int64_t b, int64_t row, int64_t col) {
-  const int64_t off = b * p.l_bs + row * p.l_rs + col;
-  if (p.ll_acc) return static_cast<const A*>(p.ll)[off];
-  return ld_scalar(static_cast<const Tin*>(p.ll) + off);
+__device__ __forceinline__ A get_ll(const Img2& im, int64_t row, int64_t col) {
+  const int64_t off = row * im.l_rs + col;
+  if (im.ll_acc) return static_cast<const A*>(im.ll)[off];
+  return ld_scalar(static_cast<const Tin*>(im.ll) + off);
 }
 
 // ---------------------------------------------------------------------------
-// Analysis.  Block of warps: 1 x 8 (32 x 256 px) for L <= 5, 2 x 4 (64 x 128)
-// for L = 6.
+// Analysis of one 32 x 32 block by one warp: levels 1..min(L, 5), every
+// band stored; returns LL5 (used by a sixth level when L = 6).
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout, int L>
-__global__ void __launch_bounds__(256) k_dwt2d_fast(const Pass p) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, int64_t y0,
+                                                                int64_t x0, int lane) {
   using A = typename AccT<Tin>::type;
-  static_assert(L >= 1 && L <= 6, "fast analysis fuses 1..6 levels");
-  constexpr int WR = (L == 6) ? 2 : 1;
-  constexpr int WC = 8 / WR;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  static_assert(L >= 1 && L <= 6, "one warp fuses 1..6 levels");
   const int tx = lane & 3, ty = lane >> 2;
-  const int64_t per = p.tiles_x * p.tiles_y;
-  const int64_t t = blockIdx.x;
-  const int64_t b = t / per, rr = t - b * per;
-  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
-  const int64_t y0 = cy * (32 * WR) + (warp / WC) * 32;
-  const int64_t x0 = cx * (32 * WC) + (warp % WC) * 32;
-  const bool active = (y0 < p.h) && (x0 < p.w);
-  const Bands<Tout> out{static_cast<Tout*>(p.dst) + b * p.d_bs, p.d_rs, p.h, p.w};
+  const Bands<Tout> out{static_cast<Tout*>(im.dst), im.d_rs, im.h, im.w};
   const int64_t py = y0 + 4 * ty, px = x0 + 8 * tx;
   A l5 = A(0);
 
-  if (active) {
-    const Tin* src = static_cast<const Tin*>(p.src) + b * p.s_bs + py * p.s_rs + px;
-    A v[4][8];
+  const Tin* src = static_cast<const Tin*>(im.src) + py * im.s_rs + px;
+  A v[4][8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) load8(src + r * p.s_rs, v[r]);
+  for (int r = 0; r < 4; ++r) load8(src + r * im.s_rs, v[r]);
 
-    // ---- level 1: eight 2x2 blocks per lane ----
-    A l1[2][4];
+  // ---- level 1: eight 2x2 blocks per lane ----
+  A l1[2][4];
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp) {
+    A hx[4], hy[4], hh[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      fwd_quad(v[2 * rp][2 * c], v[2 * rp][2 * c + 1], v[2 * rp + 1][2 * c],
+               v[2 * rp + 1][2 * c + 1], l1[rp][c], hx[c], hy[c], hh[c]);
+    const int64_t row = (py >> 1) + rp, col = px >> 1;
+    store4(out.hx(1, row, col), hx);
+    store4(out.hy(1, row, col), hy);
+    store4(out.hh(1, row, col), hh);
+  }
+  if constexpr (L == 1) {
 #pragma unroll
     for (int rp = 0; rp < 2; ++rp) {
-      A hx[4], hy[4], hh[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        fwd_quad(v[2 * rp][2 * c], v[2 * rp][2 * c + 1], v[2 * rp + 1][2 * c],
-                 v[2 * rp + 1][2 * c + 1], l1[rp][c], hx[c], hy[c], hh[c]);
       const int64_t row = (py >> 1) + rp, col = px >> 1;
-      store4(out.hx(1, row, col), hx);
-      store4(out.hy(1, row, col), hy);
-      store4(out.hh(1, row, col), hh);
+      if (!im.ll_acc) {
+        store4(static_cast<Tout*>(im.ll) + row * im.l_rs + col, l1[rp]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) put_ll<Tout>(im, row, col + c, l1[rp][c]);
+      }
     }
-    if constexpr (L == 1) {
+  } else {
+    // ---- level 2: two 2x2 blocks of LL1 per lane ----
+    A l2[2];
+    {
+      A hx[2], hy[2], hh[2];
 #pragma unroll
-      for (int rp = 0; rp < 2; ++rp) {
-        const int64_t row = (py >> 1) + rp, col = px >> 1;
-        if (!p.ll_acc) {
-          store4(static_cast<Tout*>(p.ll) + b * p.l_bs + row * p.l_rs + col, l1[rp]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) put_ll<Tout>(p, b, row, col + c, l1[rp][c]);
-        }
+      for (int c = 0; c < 2; ++c)
+        fwd_quad(l1[0][2 * c], l1[0][2 * c + 1], l1[1][2 * c], l1[1][2 * c + 1], l2[c], hx[c],
+                 hy[c], hh[c]);
+      const int64_t row = py >> 2, col = px >> 2;
+      store2(out.hx(2, row, col), hx);
+      store2(out.hy(2, row, col), hy);
+      store2(out.hh(2, row, col), hh);
+    }
+    if constexpr (L == 2) {
+      const int64_t row = py >> 2, col = px >> 2;
+      if (!im.ll_acc) {
+        store2(static_cast<Tout*>(im.ll) + row * im.l_rs + col, l2);
+      } else {
+        put_ll<Tout>(im, row, col, l2[0]);
+        put_ll<Tout>(im, row, col + 1, l2[1]);
       }
     } else {
-      // ---- level 2: two 2x2 blocks of LL1 per lane ----
-      A l2[2];
-      {
-        A hx[2], hy[2], hh[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-          fwd_quad(l1[0][2 * c], l1[0][2 * c + 1], l1[1][2 * c], l1[1][2 * c + 1], l2[c], hx[c],
-                   hy[c], hh[c]);
-        const int64_t row = py >> 2, col = px >> 2;
-        store2(out.hx(2, row, col), hx);
-        store2(out.hy(2, row, col), hy);
-        store2(out.hh(2, row, col), hh);
+      // ---- level 3: horizontal pair in the lane, vertical pair lane^4 ----
+      A l3, x3, y3, z3;
+      vpair(l2[0] + l2[1], l2[1] - l2[0], (ty & 1) != 0, 4, l3, x3, y3, z3);
+      const int64_t r3 = py >> 3, c3 = px >> 3;
+      const bool own3 = (ty & 1) == 0;
+      if (own3) {
+        st_scalar(out.hx(3, r3, c3), x3);
+        st_scalar(out.hy(3, r3, c3), y3);
+        st_scalar(out.hh(3, r3, c3), z3);
       }
-      if constexpr (L == 2) {
-        const int64_t row = py >> 2, col = px >> 2;
-        if (!p.ll_acc) {
-          store2(static_cast<Tout*>(p.ll) + b * p.l_bs + row * p.l_rs + col, l2);
-        } else {
-          put_ll<Tout>(p, b, row, col, l2[0]);
-          put_ll<Tout>(p, b, row, col + 1, l2[1]);
-        }
+      if constexpr (L == 3) {
+        if (own3) put_ll<Tout>(im, r3, c3, l3);
       } else {
-        // ---- level 3: horizontal pair in the lane, vertical pair lane^4 ----
-        A l3, x3, y3, z3;
-        vpair(l2[0] + l2[1], l2[1] - l2[0], (ty & 1) != 0, 4, l3, x3, y3, z3);
-        const int64_t r3 = py >> 3, c3 = px >> 3;
-        const bool own3 = (ty & 1) == 0;
-        if (own3) {
-          st_scalar(out.hx(3, r3, c3), x3);
-          st_scalar(out.hy(3, r3, c3), y3);
-          st_scalar(out.hh(3, r3, c3), z3);
+        // ---- level 4: pairs lane^1 (columns) and lane^8 (rows) ----
+        A lo, hi, l4, x4, y4, z4;
+        hpair(l3, (tx & 1) != 0, 1, lo, hi);
+        vpair(lo, hi, ((ty >> 1) & 1) != 0, 8, l4, x4, y4, z4);
+        const int64_t r4 = py >> 4, c4 = px >> 4;
+        const bool own4 = (ty & 3) == 0 && (tx & 1) == 0;
+        if (own4) {
+          st_scalar(out.hx(4, r4, c4), x4);
+          st_scalar(out.hy(4, r4, c4), y4);
+          st_scalar(out.hh(4, r4, c4), z4);
         }
-        if constexpr (L == 3) {
-          if (own3) put_ll<Tout>(p, b, r3, c3, l3);
+        if constexpr (L == 4) {
+          if (own4) put_ll<Tout>(im, r4, c4, l4);
         } else {
-          // ---- level 4: pairs lane^1 (columns) and lane^8 (rows) ----
-          A lo, hi, l4, x4, y4, z4;
-          hpair(l3, (tx & 1) != 0, 1, lo, hi);
-          vpair(lo, hi, ((ty >> 1) & 1) != 0, 8, l4, x4, y4, z4);
-          const int64_t r4 = py >> 4, c4 = px >> 4;
-          const bool own4 = (ty & 3) == 0 && (tx & 1) == 0;
-          if (own4) {
-            st_scalar(out.hx(4, r4, c4), x4);
-            st_scalar(out.hy(4, r4, c4), y4);
-            st_scalar(out.hh(4, r4, c4), z4);
-          }
-          if constexpr (L == 4) {
-            if (own4) put_ll<Tout>(p, b, r4, c4, l4);
-          } else {
-            // ---- level 5: pairs lane^2 (columns) and lane^16 (rows) ----
-            A lo5, hi5, x5, y5, z5;
-            hpair(l4, (tx & 2) != 0, 2, lo5, hi5);
-            vpair(lo5, hi5, (ty & 4) != 0, 16, l5, x5, y5, z5);
-            if (lane == 0) {
-              const int64_t r5 = py >> 5, c5 = px >> 5;
-              st_scalar(out.hx(5, r5, c5), x5);
-              st_scalar(out.hy(5, r5, c5), y5);
-              st_scalar(out.hh(5, r5, c5), z5);
-              if constexpr (L == 5) put_ll<Tout>(p, b, r5, c5, l5);
-            }
+          // ---- level 5: pairs lane^2 (columns) and lane^16 (rows) ----
+          A lo5, hi5, x5, y5, z5;
+          hpair(l4, (tx & 2) != 0, 2, lo5, hi5);
+          vpair(lo5, hi5, (ty & 4) != 0, 16, l5, x5, y5, z5);
+          if (lane == 0) {
+            const int64_t r5 = py >> 5, c5 = px >> 5;
+            st_scalar(out.hx(5, r5, c5), x5);
+            st_scalar(out.hy(5, r5, c5), y5);
+            st_scalar(out.hh(5, r5, c5), z5);
+            if constexpr (L == 5) put_ll<Tout>(im, r5, c5, l5);
           }
         }
       }
     }
   }
+  return l5;
+}
 
-  if constexpr (L == 6) {
-    // ---- level 6: the four warps of each 64 x 64 block ----
-    __shared__ A s5[WR][WC];
-    if (lane == 0) s5[warp / WC][warp % WC] = l5;
-    __syncthreads();
-    if (threadIdx.x < WC / 2) {
-      const int j = threadIdx.x;
-      const int64_t by0 = cy * 64, bx0 = cx * 128 + 64 * j;
-      if (by0 < p.h && bx0 < p.w) {
-        A l6, x6, y6, z6;
-        fwd_quad(s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j], s5[1][2 * j + 1], l6, x6, y6, z6);
-        const int64_t r6 = by0 >> 6, c6 = bx0 >> 6;
-        st_scalar(out.hx(6, r6, c6), x6);
-        st_scalar(out.hy(6, r6, c6), y6);
-        st_scalar(out.hh(6, r6, c6), z6);
-        put_ll<Tout>(p, b, r6, c6, l6);
-      }
-    }
-  }
+// Level 6 of one 64 x 64 block from the LL5 of its four 32 x 32 blocks.
+template <typename Tout, typename A>
+__device__ __forceinline__ void dwt_level6(const Img2& im, A tl, A tr, A bl, A br, int64_t by0,
+                                           int64_t bx0) {
+  const Bands<Tout> out{static_cast<Tout*>(im.dst), im.d_rs, im.h, im.w};
+  A l6, x6, y6, z6;
+  fwd_quad(tl, tr, bl, br, l6, x6, y6, z6);
+  const int64_t r6 = by0 >> 6, c6 = bx0 >> 6;
+  st_scalar(out.hx(6, r6, c6), x6);
+  st_scalar(out.hy(6, r6, c6), y6);
+  st_scalar(out.hh(6, r6, c6), z6);
+  put_ll<Tout>(im, r6, c6, l6);
 }
 
 // ---------------------------------------------------------------------------
-// Synthesis.  Block of warps: 1 x 8 (32 x 256 px) for every L.
+// Synthesis of one 32 x 32 block by one warp (any L <= 6): every load is
+// issued first; no communication between lanes.
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout, int L>
-__global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
-  pdl_wait();
-  pdl_trigger();
+__device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t x0, int lane) {
   using A = typename AccT<Tin>::type;
-  static_assert(L >= 1 && L <= 6, "fast synthesis fuses 1..6 levels");
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  static_assert(L >= 1 && L <= 6, "one warp undoes 1..6 levels");
   const int tx = lane & 3, ty = lane >> 2;
-  const int64_t per = p.tiles_x * p.tiles_y;
-  const int64_t t = blockIdx.x;
-  const int64_t b = t / per, rr = t - b * per;
-  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
-  const int64_t y0 = cy * 32, x0 = cx * 256 + warp * 32;
-  if (y0 >= p.h || x0 >= p.w) return;
-  const Bands<const Tin> in{static_cast<const Tin*>(p.src) + b * p.s_bs, p.s_rs, p.h, p.w};
+  const Bands<const Tin> in{static_cast<const Tin*>(im.src), im.s_rs, im.h, im.w};
   const int64_t py = y0 + 4 * ty, px = x0 + 8 * tx;
 
-  // ---- every load first ----
   A d1x[2][4], d1y[2][4], d1z[2][4];
 #pragma unroll
   for (int rp = 0; rp < 2; ++rp) {
@@ -272,11 +258,11 @@ __global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
 #pragma unroll
     for (int rp = 0; rp < 2; ++rp) {
       const int64_t row = (py >> 1) + rp, col = px >> 1;
-      if (!p.ll_acc) {
-        load4(static_cast<const Tin*>(p.ll) + b * p.l_bs + row * p.l_rs + col, ll1[rp]);
+      if (!im.ll_acc) {
+        load4(static_cast<const Tin*>(im.ll) + row * im.l_rs + col, ll1[rp]);
       } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) ll1[rp][c] = get_ll<Tin, A>(p, b, row, col + c);
+        for (int c = 0; c < 4; ++c) ll1[rp][c] = get_ll<Tin, A>(im, row, col + c);
       }
     }
   } else {
@@ -285,11 +271,11 @@ __global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
     load2(in.hy(2, row, col), d2y);
     load2(in.hh(2, row, col), d2z);
     if constexpr (L == 2) {
-      if (!p.ll_acc) {
-        load2(static_cast<const Tin*>(p.ll) + b * p.l_bs + row * p.l_rs + col, ll2);
+      if (!im.ll_acc) {
+        load2(static_cast<const Tin*>(im.ll) + row * im.l_rs + col, ll2);
       } else {
-        ll2[0] = get_ll<Tin, A>(p, b, row, col);
-        ll2[1] = get_ll<Tin, A>(p, b, row, col + 1);
+        ll2[0] = get_ll<Tin, A>(im, row, col);
+        ll2[1] = get_ll<Tin, A>(im, row, col + 1);
       }
     } else {
 #pragma unroll
@@ -299,7 +285,7 @@ __global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
         cyv[l] = ld_scalar(in.hy(l, r, c));
         czv[l] = ld_scalar(in.hh(l, r, c));
       }
-      llL = get_ll<Tin, A>(p, b, py >> L, px >> L);
+      llL = get_ll<Tin, A>(im, py >> L, px >> L);
     }
   }
 
@@ -322,7 +308,7 @@ __global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
                ll1[1][2 * c + 1]);
   }
   // ---- level 1: the 4 x 8 micro-block ----
-  Tout* dst = static_cast<Tout*>(p.dst) + b * p.d_bs + py * p.d_rs + px;
+  Tout* dst = static_cast<Tout*>(im.dst) + py * im.d_rs + px;
 #pragma unroll
   for (int rp = 0; rp < 2; ++rp) {
     A o0[8], o1[8];
@@ -330,9 +316,75 @@ __global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
     for (int c = 0; c < 4; ++c)
       inv_quad(ll1[rp][c], d1x[rp][c], d1y[rp][c], d1z[rp][c], o0[2 * c], o0[2 * c + 1],
                o1[2 * c], o1[2 * c + 1]);
-    store8(dst + (2 * rp) * p.d_rs, o0);
-    store8(dst + (2 * rp + 1) * p.d_rs, o1);
+    store8(dst + (2 * rp) * im.d_rs, o0);
+    store8(dst + (2 * rp + 1) * im.d_rs, o1);
   }
+}
+
+template <typename Tin, typename Tout>
+__device__ __forceinline__ Img2 pass_image(const Pass& p, int64_t b) {
+  using A = typename AccT<Tin>::type;
+  Img2 im;
+  im.src = static_cast<const Tin*>(p.src) + b * p.s_bs;
+  im.s_rs = p.s_rs;
+  im.dst = static_cast<Tout*>(p.dst) + b * p.d_bs;
+  im.d_rs = p.d_rs;
+  im.ll = p.ll_acc ? (void*)(static_cast<A*>(p.ll) + b * p.l_bs)
+                   : (void*)(static_cast<Tout*>(p.ll) + b * p.l_bs);
+  im.l_rs = p.l_rs;
+  im.ll_acc = p.ll_acc;
+  im.h = p.h;
+  im.w = p.w;
+  return im;
+}
+
+// ---------------------------------------------------------------------------
+// Strided-batch kernels.  Analysis block of warps: 1 x 8 (32 x 256 px) for
+// L <= 5, 2 x 4 (64 x 128 px) for L = 6.  Synthesis: 1 x 8 for every L.
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout, int L>
+__global__ void __launch_bounds__(256) k_dwt2d_fast(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename AccT<Tin>::type;
+  constexpr int WR = (L == 6) ? 2 : 1;
+  constexpr int WC = 8 / WR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t per = p.tiles_x * p.tiles_y;
+  const int64_t t = blockIdx.x;
+  const int64_t b = t / per, rr = t - b * per;
+  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
+  const int64_t y0 = cy * (32 * WR) + (warp / WC) * 32;
+  const int64_t x0 = cx * (32 * WC) + (warp % WC) * 32;
+  const Img2 im = pass_image<Tin, Tout>(p, b);
+  A l5 = A(0);
+  if (y0 < p.h && x0 < p.w) l5 = dwt_block32<Tin, Tout, L>(im, y0, x0, lane);
+  if constexpr (L == 6) {
+    __shared__ A s5[WR][WC];
+    if (lane == 0) s5[warp / WC][warp % WC] = l5;
+    __syncthreads();
+    if (threadIdx.x < WC / 2) {
+      const int j = threadIdx.x;
+      const int64_t by0 = cy * 64, bx0 = cx * 128 + 64 * j;
+      if (by0 < p.h && bx0 < p.w)
+        dwt_level6<Tout>(im, s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j], s5[1][2 * j + 1],
+                         by0, bx0);
+    }
+  }
+}
+
+template <typename Tin, typename Tout, int L>
+__global__ void __launch_bounds__(256) k_idwt2d_fast(const Pass p) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t per = p.tiles_x * p.tiles_y;
+  const int64_t t = blockIdx.x;
+  const int64_t b = t / per, rr = t - b * per;
+  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
+  const int64_t y0 = cy * 32, x0 = cx * 256 + warp * 32;
+  if (y0 >= p.h || x0 >= p.w) return;
+  idwt_block32<Tin, Tout, L>(pass_image<Tin, Tout>(p, b), y0, x0, lane);
 }
 
 template <typename Tin, typename Tout>

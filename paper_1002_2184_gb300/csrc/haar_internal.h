@@ -58,6 +58,45 @@ constexpr int kScalarTileLevels = 6;
 enum Chunk1Cfg { kC1024 = 0, kC4096 = 1 };
 inline int chunk_max_levels(int cfg) { return cfg == kC1024 ? 10 : 12; }
 
+// ---------------------------------------------------------------------------
+// Ragged batches (one persistent launch over images of different sizes).
+// ---------------------------------------------------------------------------
+struct RaggedImg {
+  int64_t in_off, out_off;  // element offsets from the batch base pointers
+  int64_t h, w;
+  int64_t in_rs, out_rs;
+  int64_t unit_begin;       // first work unit of this image
+  int32_t levels, units_x;
+};
+
+// Workspace header (device): the unit counter, the count of finished blocks,
+// the count of units transformed and an error word; the image table follows
+// at kRaggedTableOffset.
+struct RaggedHeader {
+  unsigned long long next_unit;
+  unsigned long long blocks_done;
+  unsigned long long units_done;
+  unsigned long long error;
+};
+constexpr size_t kRaggedTableOffset = 256;
+
+struct RaggedArgs {
+  RaggedHeader* hdr;
+  const RaggedImg* imgs;
+  int64_t n_imgs;
+  int64_t total_units;
+  const void* in;
+  void* out;
+};
+
+// Work-unit shapes (eight 32 x 32 warp blocks).
+enum RaggedUnit { kUnit64x128 = 0, kUnit32x256 = 1 };
+inline int unit_h(int u) { return u == kUnit64x128 ? 64 : 32; }
+inline int unit_w(int u) { return u == kUnit64x128 ? 128 : 256; }
+
+// Records the cudaError_t reported by haar_last_cuda_error() (per host thread).
+void set_last_cuda_error(int e);
+
 // Launchers.  Return cudaErrorInvalidValue for an unsupported dtype pair.
 // grid_cap <= 0 means one block per tile.
 cudaError_t launch_dwt2d(int tin, int tout, Pass p, int tile_cfg, bool vec, int grid_cap,
@@ -74,7 +113,9 @@ cudaError_t launch_idwt1d(int tin, int tout, Pass p, int chunk_cfg, bool vec, cu
   cudaError_t launch_idwt2d_##NAME(int tout, Pass p, int tile_cfg, bool vec, int grid_cap,    \
                                    cudaStream_t s);                                            \
   cudaError_t launch_dwt1d_##NAME(int tout, Pass p, int chunk_cfg, bool vec, cudaStream_t s); \
-  cudaError_t launch_idwt1d_##NAME(int tout, Pass p, int chunk_cfg, bool vec, cudaStream_t s);
+  cudaError_t launch_idwt1d_##NAME(int tout, Pass p, int chunk_cfg, bool vec, cudaStream_t s); \
+  cudaError_t launch_ragged_##NAME(int tout, bool fwd, const RaggedArgs& a, int unit,        \
+                                   unsigned grid, cudaStream_t s);
 FH_DECL_TIN(f32)
 FH_DECL_TIN(bf16)
 FH_DECL_TIN(f16)

@@ -4,6 +4,7 @@
 
 #include "haar_internal.h"
 #include "haar_fast2d.cuh"
+#include "haar_ragged.cuh"
 #include "haar_kernels.cuh"
 
 namespace fh {

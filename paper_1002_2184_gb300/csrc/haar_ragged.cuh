@@ -1,0 +1,190 @@
+// haar_ragged.cuh -- one persistent launch over a ragged batch of images of
+// different sizes and level counts.
+//
+// The work is cut into units of UH x UW pixels (8 warps, one 32 x 32 block
+// per warp, the same per-warp bodies as the strided-batch kernels).  A plan
+// lists, per image, its first unit index; blocks take units from a global
+// atomic counter, find the image by binary search, and transform.  The last
+// block to finish resets the counter, so the launch can be replayed (for
+// instance from a CUDA graph) without any host work; it also checks that
+// every unit was handed out exactly once and records an error word if not.
+#pragma once
+
+#include <type_traits>
+
+#include "haar_fast2d.cuh"
+#include "haar_internal.h"
+
+namespace fh {
+
+// Takes the next unit; returns its index (>= total when the queue is empty)
+// and the image it belongs to (shared by the whole block).
+__device__ __forceinline__ long long ragged_next(const RaggedArgs& a, long long* s_unit,
+                                                 int* s_img, int& img_out) {
+  if (threadIdx.x == 0) {
+    const long long u = (long long)atomicAdd(&a.hdr->next_unit, 1ull);
+    int img = -1;
+    if (u < a.total_units) {
+      int64_t lo = 0, hi = a.n_imgs - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (a.imgs[mid].unit_begin <= u)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      img = (int)lo;
+    }
+    *s_unit = u;
+    *s_img = img;
+  }
+  __syncthreads();
+  const long long u = *s_unit;
+  img_out = *s_img;
+  __syncthreads();  // nobody may refill s_unit / s_img before everyone read them
+  return u;
+}
+
+// Called once per block after its loop, with the number of units it
+// transformed.  The last block to finish checks that every unit was
+// transformed exactly once and that the queue ran out exactly when expected,
+// records an error word otherwise, and resets the counters for the next
+// launch.
+__device__ __forceinline__ void ragged_finish(const RaggedArgs& a, long long mine) {
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.hdr->units_done, (unsigned long long)mine);
+    __threadfence();
+    const unsigned long long d = atomicAdd(&a.hdr->blocks_done, 1ull);
+    if (d == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long total = (unsigned long long)a.total_units;
+      const unsigned long long done = atomicAdd(&a.hdr->units_done, 0ull);
+      const unsigned long long next = atomicAdd(&a.hdr->next_unit, 0ull);
+      if (done != total || next != total + gridDim.x) atomicExch(&a.hdr->error, 1ull);
+      atomicExch(&a.hdr->next_unit, 0ull);
+      atomicExch(&a.hdr->units_done, 0ull);
+      atomicExch(&a.hdr->blocks_done, 0ull);
+    }
+  }
+}
+
+template <typename Tin, typename Tout>
+__device__ __forceinline__ Img2 ragged_image(const RaggedArgs& a, const RaggedImg& r) {
+  Img2 im;
+  im.src = static_cast<const Tin*>(a.in) + r.in_off;
+  im.s_rs = r.in_rs;
+  im.dst = static_cast<Tout*>(a.out) + r.out_off;
+  im.d_rs = r.out_rs;
+  im.h = r.h;
+  im.w = r.w;
+  return im;
+}
+
+template <typename Tin, typename Tout, int UH, int UW>
+__global__ void __launch_bounds__(256) k_ragged_dwt2d(const RaggedArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename AccT<Tin>::type;
+  constexpr int WR = UH / 32, WC = UW / 32;
+  static_assert(WR * WC == 8, "a unit is eight 32 x 32 blocks");
+  __shared__ long long s_unit;
+  __shared__ int s_img;
+  __shared__ A s5[WR][WC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t limit = a.total_units + gridDim.x;  // the queue hands out at most this many
+  long long mine = 0;
+  for (int64_t it = 0; it < limit; ++it) {
+    int img;
+    const long long u = ragged_next(a, &s_unit, &s_img, img);
+    if (u >= a.total_units) break;
+    ++mine;
+    const RaggedImg r = a.imgs[img];
+    Img2 im = ragged_image<Tin, Tout>(a, r);
+    im.ll = im.dst;
+    im.l_rs = im.d_rs;
+    im.ll_acc = 0;
+    const int64_t local = u - r.unit_begin;
+    const int64_t uy = local / r.units_x, ux = local - uy * r.units_x;
+    const int64_t y0 = uy * UH + (warp / WC) * 32, x0 = ux * UW + (warp % WC) * 32;
+    const bool act = y0 < r.h && x0 < r.w;
+    switch (r.levels) {
+      case 1: if (act) dwt_block32<Tin, Tout, 1>(im, y0, x0, lane); break;
+      case 2: if (act) dwt_block32<Tin, Tout, 2>(im, y0, x0, lane); break;
+      case 3: if (act) dwt_block32<Tin, Tout, 3>(im, y0, x0, lane); break;
+      case 4: if (act) dwt_block32<Tin, Tout, 4>(im, y0, x0, lane); break;
+      case 5: if (act) dwt_block32<Tin, Tout, 5>(im, y0, x0, lane); break;
+      case 6:
+        if constexpr (WR == 2) {
+          const A l5 = act ? dwt_block32<Tin, Tout, 6>(im, y0, x0, lane) : A(0);
+          if (lane == 0) s5[warp / WC][warp % WC] = l5;
+          __syncthreads();
+          if (threadIdx.x < WC / 2) {
+            const int j = threadIdx.x;
+            const int64_t by0 = uy * 64, bx0 = ux * UW + 64 * j;
+            if (by0 < r.h && bx0 < r.w)
+              dwt_level6<Tout>(im, s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j],
+                               s5[1][2 * j + 1], by0, bx0);
+          }
+        }
+        break;
+      default: break;
+    }
+  }
+  ragged_finish(a, mine);
+}
+
+template <typename Tin, typename Tout, int UH, int UW>
+__global__ void __launch_bounds__(256) k_ragged_idwt2d(const RaggedArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int WC = UW / 32;
+  __shared__ long long s_unit;
+  __shared__ int s_img;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t limit = a.total_units + gridDim.x;
+  long long mine = 0;
+  for (int64_t it = 0; it < limit; ++it) {
+    int img;
+    const long long u = ragged_next(a, &s_unit, &s_img, img);
+    if (u >= a.total_units) break;
+    ++mine;
+    const RaggedImg r = a.imgs[img];
+    Img2 im = ragged_image<Tin, Tout>(a, r);
+    im.ll = const_cast<void*>(im.src);
+    im.l_rs = im.s_rs;
+    im.ll_acc = 0;
+    const int64_t local = u - r.unit_begin;
+    const int64_t uy = local / r.units_x, ux = local - uy * r.units_x;
+    const int64_t y0 = uy * UH + (warp / WC) * 32, x0 = ux * UW + (warp % WC) * 32;
+    if (y0 < r.h && x0 < r.w) {
+      switch (r.levels) {
+        case 1: idwt_block32<Tin, Tout, 1>(im, y0, x0, lane); break;
+        case 2: idwt_block32<Tin, Tout, 2>(im, y0, x0, lane); break;
+        case 3: idwt_block32<Tin, Tout, 3>(im, y0, x0, lane); break;
+        case 4: idwt_block32<Tin, Tout, 4>(im, y0, x0, lane); break;
+        case 5: idwt_block32<Tin, Tout, 5>(im, y0, x0, lane); break;
+        case 6: idwt_block32<Tin, Tout, 6>(im, y0, x0, lane); break;
+        default: break;
+      }
+    }
+  }
+  ragged_finish(a, mine);
+}
+
+template <typename Tin, typename Tout>
+cudaError_t ragged_t(bool fwd, const RaggedArgs& a, int unit, unsigned grid, cudaStream_t s) {
+  if (a.total_units == 0 || grid == 0) return cudaSuccess;
+  if (fwd) {
+    if (unit == kUnit64x128) return launch_pdl(k_ragged_dwt2d<Tin, Tout, 64, 128>, grid, 256, s, a);
+    return launch_pdl(k_ragged_dwt2d<Tin, Tout, 32, 256>, grid, 256, s, a);
+  }
+  if constexpr (std::is_same<Tin, uint8_t>::value) {
+    return cudaErrorInvalidValue;  // coefficients are never stored as uint8
+  } else {
+    if (unit == kUnit64x128)
+      return launch_pdl(k_ragged_idwt2d<Tin, Tout, 64, 128>, grid, 256, s, a);
+    return launch_pdl(k_ragged_idwt2d<Tin, Tout, 32, 256>, grid, 256, s, a);
+  }
+}
+
+}  // namespace fh

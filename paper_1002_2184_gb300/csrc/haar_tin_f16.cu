@@ -27,4 +27,11 @@ cudaError_t launch_idwt1d_f16(int tout, Pass p, int cfg, bool vec, cudaStream_t 
                         (idwt1d_t<__half, __half>(p, cfg, vec, s)))
 }
 
+cudaError_t launch_ragged_f16(int tout, bool fwd, const RaggedArgs& a, int unit, unsigned grid,
+                             cudaStream_t s) {
+  FH_TOUT_SWITCH_FLOATS((ragged_t<__half, float>(fwd, a, unit, grid, s)),
+                        (ragged_t<__half, __nv_bfloat16>(fwd, a, unit, grid, s)),
+                        (ragged_t<__half, __half>(fwd, a, unit, grid, s)))
+}
+
 }  // namespace fh

@@ -23,4 +23,10 @@ cudaError_t launch_idwt1d_f64(int tout, Pass p, int cfg, bool vec, cudaStream_t 
   return idwt1d_t<double, double>(p, cfg, vec, s);
 }
 
+cudaError_t launch_ragged_f64(int tout, bool fwd, const RaggedArgs& a, int unit, unsigned grid,
+                             cudaStream_t s) {
+  if (tout != kF64) return cudaErrorInvalidValue;
+  return ragged_t<double, double>(fwd, a, unit, grid, s);
+}
+
 }  // namespace fh

@@ -24,4 +24,12 @@ cudaError_t launch_idwt1d_u8(int, Pass, int, bool, cudaStream_t) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_ragged_u8(int tout, bool fwd, const RaggedArgs& a, int unit, unsigned grid,
+                            cudaStream_t s) {
+  if (!fwd) return cudaErrorInvalidValue;
+  FH_TOUT_SWITCH_FLOATS((ragged_t<uint8_t, float>(true, a, unit, grid, s)),
+                        (ragged_t<uint8_t, __nv_bfloat16>(true, a, unit, grid, s)),
+                        (ragged_t<uint8_t, __half>(true, a, unit, grid, s)))
+}
+
 }  // namespace fh

@@ -127,3 +127,66 @@ def test_workspace_sizes(lib):
     assert call(lib, "haar_dwt_2d", src, d(B, h=4096, w=4096), 7,
                 ws=1 << 41, wsb=100) == L.HAAR_EWORKSPACE
     assert lib.haar_workspace_size(9, ctypes.byref(src), 1, ctypes.byref(n)) == L.HAAR_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# Ragged plans: host-only validation (no device call is made by these).
+# ---------------------------------------------------------------------------
+def _items(spec):
+    from paper_1002_2184_gb300 import _lib as L
+    arr = (L.HaarRaggedItem * max(1, len(spec)))()
+    off = 0
+    for i, (h, w, lv) in enumerate(spec):
+        arr[i] = L.HaarRaggedItem(off, off, h, w, w, w, lv, 0)
+        off += h * w
+    return arr
+
+
+def _create(lib, spec, unit=0, bps=4):
+    h = ctypes.c_void_p()
+    rc = lib.haar_ragged_plan_create(_items(spec), len(spec), unit, bps, ctypes.byref(h))
+    return rc, h
+
+
+def test_ragged_plan_validation(lib):
+    from paper_1002_2184_gb300 import _lib as L
+    assert _create(lib, [(48, 64, 3)])[0] == L.HAAR_ESHAPE        # 48 % 32 != 0
+    assert _create(lib, [(64, 64, 7)])[0] == L.HAAR_EINVAL        # more than 6 levels
+    assert _create(lib, [(64, 64, 0)])[0] == L.HAAR_EINVAL
+    assert _create(lib, [(96, 64, 6)])[0] == L.HAAR_ESHAPE        # 96 % 64 != 0
+    assert _create(lib, [(64, 64, 6)], unit=1)[0] == L.HAAR_ESHAPE  # 6 levels need 64 x 128
+    assert _create(lib, [(64, 64, 3)], unit=7)[0] == L.HAAR_EINVAL
+    assert _create(lib, [(64, 64, 3)], bps=0)[0] == L.HAAR_EINVAL
+    bad = _items([(64, 64, 3)])
+    bad[0].in_row_stride = 32
+    assert lib.haar_ragged_plan_create(bad, 1, 0, 4, ctypes.byref(ctypes.c_void_p())) \
+        == L.HAAR_EINVAL
+
+
+def test_ragged_plan_geometry(lib):
+    from paper_1002_2184_gb300 import _lib as L
+    spec = [(64, 128, 6), (64, 64, 3), (128, 256, 5), (32, 32, 1)]
+    rc, h = _create(lib, spec)
+    assert rc == L.HAAR_OK
+    units, px = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.haar_ragged_plan_info(h, ctypes.byref(units), ctypes.byref(px), None) == 0
+    # 64 x 128 units: 1 + 1 + 2*2 + 1
+    assert units.value == 7
+    assert px.value == sum(a * b for a, b, _ in spec)
+    n = ctypes.c_size_t()
+    assert lib.haar_ragged_workspace_size(h, ctypes.byref(n)) == 0
+    assert n.value >= 256 + 64 * len(spec) and n.value % 256 == 0
+    # argument checks that run before any device work
+    A, B = 1 << 40, 1 << 41
+    assert lib.haar_dwt_2d_ragged(h, A, 0, B, 3, 1 << 42, n.value, None) == L.HAAR_EDTYPE
+    assert lib.haar_idwt_2d_ragged(h, A, 3, B, 0, 1 << 42, n.value, None) == L.HAAR_EDTYPE
+    assert lib.haar_dwt_2d_ragged(h, A, 0, B, 0, None, n.value, None) == L.HAAR_EWORKSPACE
+    assert lib.haar_dwt_2d_ragged(h, A, 0, B, 0, 1 << 42, 8, None) == L.HAAR_EWORKSPACE
+    assert lib.haar_dwt_2d_ragged(h, A + 4, 0, B, 0, 1 << 42, n.value, None) == L.HAAR_EINVAL
+    assert lib.haar_dwt_2d_ragged(h, A, 0, A + 1024, 0, 1 << 42, n.value, None) == L.HAAR_EALIAS
+    assert lib.haar_dwt_2d_ragged(h, None, 0, B, 0, 1 << 42, n.value, None) == L.HAAR_EINVAL
+    assert lib.haar_ragged_plan_destroy(h) == 0
+    rc, h0 = _create(lib, [])
+    assert rc == 0
+    assert lib.haar_dwt_2d_ragged(h0, None, 0, None, 0, None, 0, None) == 0  # nothing to do
+    lib.haar_ragged_plan_destroy(h0)
