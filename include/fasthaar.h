@@ -129,6 +129,26 @@ int haar_dwt_2d(const haar_desc *x, const haar_desc *coef, int levels, void *wor
 int haar_idwt_2d(const haar_desc *coef, const haar_desc *x, int levels, void *workspace,
                  size_t workspace_bytes, void *cuda_stream);
 
+/* Same as haar_dwt_2d, for callers that cannot allocate device memory (for
+ * example code running inside a host application that owns every
+ * allocation, or a loop where calling the allocator is not allowed): the
+ * scratch space that transforms deeper than six levels need is taken from a
+ * fixed 4 MiB array built into the library instead of from the caller, and
+ * the call allocates nothing.  The paper has no counterpart; this is an
+ * interface convenience.
+ *  - Every GPU that loads the library holds the 4 MiB array until exit.
+ *  - A transform whose scratch (haar_workspace_size(HAAR_OP_DWT_2D, ...))
+ *    exceeds 4 MiB is rejected with HAAR_EWORKSPACE; use haar_dwt_2d.
+ *  - The first call on each device looks the array's address up
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.  Call it with the stream's device current.
+ *  - All calls on a device share the one array and it keeps the last call's
+ *    contents (nothing in it needs to start at zero).  Calls whose kernels
+ *    overlap in time on the GPU (different streams, not ordered) race on the
+ *    array and give wrong results: keep them on one stream or order them. */
+int haar_dwt_2d_noalloc(const haar_desc *x, const haar_desc *coef, int levels,
+                        void *cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Ragged batches: many 2D images of different sizes and level counts in one
  * persistent launch.  Images live anywhere inside one input buffer and one

@@ -85,6 +85,7 @@ SIGNATURES = {
     "haar_idwt_1d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_dwt_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_idwt_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "haar_dwt_2d_noalloc": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P]),
     "haar_ragged_plan_create": (ctypes.c_int, [ctypes.POINTER(HaarRaggedItem), ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_void_p)]),
