@@ -484,7 +484,63 @@ def forms(api, synth, dev, world):
 
     res["ragged"] = ragged_form(api, synth, dev, entry["fp32"]["gsamples_s"])
     torch.cuda.empty_cache()
+    res["backward"] = grad_form(api, synth, dev)
+    torch.cuda.empty_cache()
     return res
+
+
+def grad_form(api, synth, dev):
+    """32 x 3 x 512 x 512 fp32, 3 levels: forward + backward of the wavelet
+    denoising loss, fused (graph replay and eager autograd) and composed from
+    separate differentiable ops, next to the plain fp32 DWT + IDWT round trip
+    of the same batch."""
+    import torch
+    from paper_1002_2184_gb300 import autograd as ad
+    gc_ = synth.GradBatch()
+    B, C, H, W = gc_.shape
+    imgs = [torch.from_numpy(synth.piecewise_smooth_image(H, W, gc_.seed, i).astype(np.float32))
+            for i in range(8)]
+    x = torch.stack([imgs[i % 8] for i in range(B * C)]).reshape(gc_.shape).to(dev)
+    px = x.numel()
+    L, t, lam = gc_.levels, gc_.threshold, gc_.l1_weight
+    plan = ad.DenoisePlan(x, L, t, lam)
+    plan.forward()
+    plan.backward()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.forward()
+        plan.backward()
+    ms_graph = time_ms(g.replay, 50)
+
+    xr = x.clone().requires_grad_(True)
+
+    def fused_eager():
+        xr.grad = None
+        ad.denoise_loss(xr, L, t, lam).backward()
+
+    def unfused_eager():
+        xr.grad = None
+        ad.denoise_loss_unfused(xr, L, t, lam).backward()
+
+    ms_fused = time_ms(fused_eager, 20)
+    ms_unfused = time_ms(unfused_eager, 20)
+    c = torch.empty_like(x)
+    y = torch.empty_like(x)
+    rt = api.Plan(x, c, L, y)
+    ms_rt = time_ms(lambda: (rt.dwt(), rt.idwt()), 50)
+    peaks = measured_peaks()
+    hbm = (peaks or {}).get("hbm_gbs") or 6800.0
+    gbs = 44.0 * px / (ms_graph * 1e-3) / 1e9
+    return {"workload": f"{B}x{C}x{H}x{W} fp32, {L} levels, soft threshold {t}, L1 weight {lam}",
+            "fused_graph_ms": round(ms_graph, 4),
+            "fused_graph_gsamples_s": round(px / (ms_graph * 1e-3) / 1e9, 2),
+            "fused_hbm_gbs": round(gbs, 1), "fused_frac_of_hbm": round(gbs / hbm, 4),
+            "fused_algorithmic_bytes_per_px": 44,
+            "fused_autograd_ms": round(ms_fused, 4),
+            "unfused_autograd_ms": round(ms_unfused, 4),
+            "plain_fp32_dwt_idwt_ms": round(ms_rt, 4),
+            "fwd_bwd_over_plain_round_trip": round(ms_graph / ms_rt, 3)}
 
 
 def ragged_form(api, synth, dev, dense_fp32_gsamples):

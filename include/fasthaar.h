@@ -215,6 +215,61 @@ int haar_ragged_status(const haar_ragged_plan *plan, void *workspace, int *statu
 
 int haar_ragged_plan_destroy(haar_ragged_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Verification reductions and a differentiable denoising loss built on the
+ * transform (the paper has neither: they serve checking and training).  The
+ * loss, for a contiguous batch of h x w images with an L-level transform W:
+ *   c = W x,  s = soft(c, t) = sign(c) max(|c| - t, 0),  xr = W^T s,
+ *   loss = mean((xr - x)^2) + l1_weight * mean(|s| over detail coefficients)
+ * Its gradient uses W^-1 = W^T (orthonormal bank, Section II): the adjoint
+ * of the analysis is the synthesis and vice versa.
+ * Arrays: contiguous batches (batch_stride = h*w, row_stride = w), all of
+ * one dtype, F32 or F64.
+ * ---------------------------------------------------------------------- */
+
+/* FP64 sums over n contiguous elements of a (and b, which may be NULL),
+ * accumulated into out3 (device, 3 doubles): out3[0] += sum a^2,
+ * out3[1] += sum (a-b)^2, out3[2] = max(out3[2], max |a-b|).  Any dtype. */
+int haar_norms_f64(const void *a, const void *b, int dtype, int64_t n, double *out3,
+                   void *cuda_stream);
+
+/* s = soft(c, threshold) elementwise (any layout of the Mallat coefficients
+ * of `levels` levels); l1_acc (device double, may be NULL) += sum of |s| over
+ * the detail positions. */
+int haar_soft_threshold(const haar_desc *c, const haar_desc *s, int levels, double threshold,
+                        double *l1_acc, void *cuda_stream);
+
+/* Adjoint of haar_soft_threshold with the L1 term: g_c = (g_s + l1_scale *
+ * g_l1 * sign(s) * [detail]) * [s != 0]; g_l1 is a device scalar of the
+ * dtype (NULL: no L1 term).  The subgradient at |c| <= threshold is 0. */
+int haar_soft_threshold_backward(const haar_desc *g_s, const haar_desc *s, const haar_desc *g_c,
+                                 int levels, double l1_scale, const void *g_l1,
+                                 void *cuda_stream);
+
+/* g_a = scale * g * (a - b) and g_b = -g_a (either output may be NULL; g is
+ * a device scalar of the dtype, NULL meaning 1). */
+int haar_sq_diff_backward(const haar_desc *a, const haar_desc *b, const haar_desc *g_a,
+                          const haar_desc *g_b, double scale, const void *g,
+                          void *cuda_stream);
+
+/* The loss, fused into two transform launches plus a one-thread finisher:
+ * writes s and the residual r = xr - x, and the loss value to `loss` (device
+ * scalar of the dtype).  acc2: device scratch of 2 doubles, zero on entry and
+ * left zero on return.  Sides multiples of 32, 1 <= levels <= 6, arrays
+ * 16-byte aligned (else HAAR_ESHAPE / HAAR_EINVAL). */
+int haar_denoise_forward(const haar_desc *x, const haar_desc *s, const haar_desc *r, int levels,
+                         double threshold, double l1_weight, double *acc2, void *loss,
+                         void *cuda_stream);
+
+/* Gradient of the fused loss with respect to x, from the saved s and r and
+ * the upstream gradient g_loss (device scalar of the dtype, NULL meaning 1):
+ *   g_c = (2g/n W r + l1_weight g / n_d sign(s) [detail]) [s != 0]
+ *   g_x = W^T g_c - 2g/n r
+ * in two transform launches; g_c is caller scratch of x's shape. */
+int haar_denoise_backward(const haar_desc *r, const haar_desc *s, const haar_desc *g_c,
+                          const haar_desc *g_x, int levels, double l1_weight,
+                          const void *g_loss, void *cuda_stream);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char *haar_status_string(int status);
 

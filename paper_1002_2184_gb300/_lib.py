@@ -100,6 +100,15 @@ SIGNATURES = {
                                            ctypes.c_size_t, _P]),
     "haar_ragged_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "haar_ragged_plan_destroy": (ctypes.c_int, [_P]),
+    "haar_norms_f64": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, _P, _P]),
+    "haar_soft_threshold": (ctypes.c_int, [_DP, _DP, ctypes.c_int, ctypes.c_double, _P, _P]),
+    "haar_soft_threshold_backward": (ctypes.c_int, [_DP, _DP, _DP, ctypes.c_int,
+                                                    ctypes.c_double, _P, _P]),
+    "haar_sq_diff_backward": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_double, _P, _P]),
+    "haar_denoise_forward": (ctypes.c_int, [_DP, _DP, _DP, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, _P, _P, _P]),
+    "haar_denoise_backward": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_int,
+                                             ctypes.c_double, _P, _P]),
 }
 
 

@@ -26,11 +26,11 @@ __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Launch `kernel<<<grid, block, 0, stream>>>(arg)` with programmatic stream
-// serialisation allowed (see pdl_wait).
-template <typename Arg>
-inline cudaError_t launch_pdl(void (*kernel)(Arg), unsigned grid, unsigned block,
-                              cudaStream_t stream, const Arg& arg) {
+// Launch `kernel<<<grid, block, 0, stream>>>(args...)` with programmatic
+// stream serialisation allowed (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                              cudaStream_t stream, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -41,7 +41,7 @@ inline cudaError_t launch_pdl(void (*kernel)(Arg), unsigned grid, unsigned block
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, arg);
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 
 // ---------------------------------------------------------------------------

@@ -75,6 +75,23 @@ __device__ __forceinline__ A inv_child(A ll, A hx, A hy, A hh, int qy, int qx) {
   return fma(sx, s2, s1) * A(0.5);
 }
 
+// Output epilogues.  The block functions hand every value they produce to
+// an epilogue object before it is stored: coefficients with a flag saying
+// whether they are detail (true) or low-pass (false), output pixels in rows
+// of eight.  EpiStore stores them unchanged; the fused loss pipeline
+// (haar_denoise.cu) substitutes epilogues that transform, read a second
+// array at the same position, and accumulate sums.
+struct EpiStore {
+  template <typename T, typename A>
+  __device__ __forceinline__ void c4(T* p, const A v[4], bool) { store4(p, v); }
+  template <typename T, typename A>
+  __device__ __forceinline__ void c2(T* p, const A v[2], bool) { store2(p, v); }
+  template <typename T, typename A>
+  __device__ __forceinline__ void c1(T* p, A v, bool) { st_scalar(p, v); }
+  template <typename T, typename A>
+  __device__ __forceinline__ void px8(T* p, const A v[8]) { store8(p, v); }
+};
+
 // One image of a pass (pointers already offset to the batch item).
 struct Img2 {
   const void* src;
@@ -103,13 +120,25 @@ __device__ __forceinline__ A get_ll(const Img2& im, int64_t row, int64_t col) {
   return ld_scalar(static_cast<const Tin*>(im.ll) + off);
 }
 
+// A low-pass output: through the epilogue into the coefficient array, or
+// unchanged into an accumulator-typed workspace (an intermediate band).
+template <typename Tout, typename A, typename Epi>
+__device__ __forceinline__ void put_ll_epi(const Img2& im, int64_t row, int64_t col, A v,
+                                           Epi& epi) {
+  if (im.ll_acc)
+    static_cast<A*>(im.ll)[row * im.l_rs + col] = v;
+  else
+    epi.c1(static_cast<Tout*>(im.ll) + row * im.l_rs + col, v, false);
+}
+
 // ---------------------------------------------------------------------------
 // Analysis of one 32 x 32 block by one warp: levels 1..min(L, 5), every
 // band stored; returns LL5 (used by a sixth level when L = 6).
 // ---------------------------------------------------------------------------
-template <typename Tin, typename Tout, int L>
+template <typename Tin, typename Tout, int L, typename Epi = EpiStore>
 __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, int64_t y0,
-                                                                int64_t x0, int lane) {
+                                                                int64_t x0, int lane,
+                                                                Epi&& epi = Epi()) {
   using A = typename AccT<Tin>::type;
   static_assert(L >= 1 && L <= 6, "one warp fuses 1..6 levels");
   const int tx = lane & 3, ty = lane >> 2;
@@ -132,16 +161,16 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
       fwd_quad(v[2 * rp][2 * c], v[2 * rp][2 * c + 1], v[2 * rp + 1][2 * c],
                v[2 * rp + 1][2 * c + 1], l1[rp][c], hx[c], hy[c], hh[c]);
     const int64_t row = (py >> 1) + rp, col = px >> 1;
-    store4(out.hx(1, row, col), hx);
-    store4(out.hy(1, row, col), hy);
-    store4(out.hh(1, row, col), hh);
+    epi.c4(out.hx(1, row, col), hx, true);
+    epi.c4(out.hy(1, row, col), hy, true);
+    epi.c4(out.hh(1, row, col), hh, true);
   }
   if constexpr (L == 1) {
 #pragma unroll
     for (int rp = 0; rp < 2; ++rp) {
       const int64_t row = (py >> 1) + rp, col = px >> 1;
       if (!im.ll_acc) {
-        store4(static_cast<Tout*>(im.ll) + row * im.l_rs + col, l1[rp]);
+        epi.c4(static_cast<Tout*>(im.ll) + row * im.l_rs + col, l1[rp], false);
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c) put_ll<Tout>(im, row, col + c, l1[rp][c]);
@@ -157,14 +186,14 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
         fwd_quad(l1[0][2 * c], l1[0][2 * c + 1], l1[1][2 * c], l1[1][2 * c + 1], l2[c], hx[c],
                  hy[c], hh[c]);
       const int64_t row = py >> 2, col = px >> 2;
-      store2(out.hx(2, row, col), hx);
-      store2(out.hy(2, row, col), hy);
-      store2(out.hh(2, row, col), hh);
+      epi.c2(out.hx(2, row, col), hx, true);
+      epi.c2(out.hy(2, row, col), hy, true);
+      epi.c2(out.hh(2, row, col), hh, true);
     }
     if constexpr (L == 2) {
       const int64_t row = py >> 2, col = px >> 2;
       if (!im.ll_acc) {
-        store2(static_cast<Tout*>(im.ll) + row * im.l_rs + col, l2);
+        epi.c2(static_cast<Tout*>(im.ll) + row * im.l_rs + col, l2, false);
       } else {
         put_ll<Tout>(im, row, col, l2[0]);
         put_ll<Tout>(im, row, col + 1, l2[1]);
@@ -176,12 +205,12 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
       const int64_t r3 = py >> 3, c3 = px >> 3;
       const bool own3 = (ty & 1) == 0;
       if (own3) {
-        st_scalar(out.hx(3, r3, c3), x3);
-        st_scalar(out.hy(3, r3, c3), y3);
-        st_scalar(out.hh(3, r3, c3), z3);
+        epi.c1(out.hx(3, r3, c3), x3, true);
+        epi.c1(out.hy(3, r3, c3), y3, true);
+        epi.c1(out.hh(3, r3, c3), z3, true);
       }
       if constexpr (L == 3) {
-        if (own3) put_ll<Tout>(im, r3, c3, l3);
+        if (own3) put_ll_epi<Tout>(im, r3, c3, l3, epi);
       } else {
         // ---- level 4: pairs lane^1 (columns) and lane^8 (rows) ----
         A lo, hi, l4, x4, y4, z4;
@@ -190,12 +219,12 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
         const int64_t r4 = py >> 4, c4 = px >> 4;
         const bool own4 = (ty & 3) == 0 && (tx & 1) == 0;
         if (own4) {
-          st_scalar(out.hx(4, r4, c4), x4);
-          st_scalar(out.hy(4, r4, c4), y4);
-          st_scalar(out.hh(4, r4, c4), z4);
+          epi.c1(out.hx(4, r4, c4), x4, true);
+          epi.c1(out.hy(4, r4, c4), y4, true);
+          epi.c1(out.hh(4, r4, c4), z4, true);
         }
         if constexpr (L == 4) {
-          if (own4) put_ll<Tout>(im, r4, c4, l4);
+          if (own4) put_ll_epi<Tout>(im, r4, c4, l4, epi);
         } else {
           // ---- level 5: pairs lane^2 (columns) and lane^16 (rows) ----
           A lo5, hi5, x5, y5, z5;
@@ -203,10 +232,10 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
           vpair(lo5, hi5, (ty & 4) != 0, 16, l5, x5, y5, z5);
           if (lane == 0) {
             const int64_t r5 = py >> 5, c5 = px >> 5;
-            st_scalar(out.hx(5, r5, c5), x5);
-            st_scalar(out.hy(5, r5, c5), y5);
-            st_scalar(out.hh(5, r5, c5), z5);
-            if constexpr (L == 5) put_ll<Tout>(im, r5, c5, l5);
+            epi.c1(out.hx(5, r5, c5), x5, true);
+            epi.c1(out.hy(5, r5, c5), y5, true);
+            epi.c1(out.hh(5, r5, c5), z5, true);
+            if constexpr (L == 5) put_ll_epi<Tout>(im, r5, c5, l5, epi);
           }
         }
       }
@@ -216,25 +245,26 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
 }
 
 // Level 6 of one 64 x 64 block from the LL5 of its four 32 x 32 blocks.
-template <typename Tout, typename A>
+template <typename Tout, typename A, typename Epi = EpiStore>
 __device__ __forceinline__ void dwt_level6(const Img2& im, A tl, A tr, A bl, A br, int64_t by0,
-                                           int64_t bx0) {
+                                           int64_t bx0, Epi&& epi = Epi()) {
   const Bands<Tout> out{static_cast<Tout*>(im.dst), im.d_rs, im.h, im.w};
   A l6, x6, y6, z6;
   fwd_quad(tl, tr, bl, br, l6, x6, y6, z6);
   const int64_t r6 = by0 >> 6, c6 = bx0 >> 6;
-  st_scalar(out.hx(6, r6, c6), x6);
-  st_scalar(out.hy(6, r6, c6), y6);
-  st_scalar(out.hh(6, r6, c6), z6);
-  put_ll<Tout>(im, r6, c6, l6);
+  epi.c1(out.hx(6, r6, c6), x6, true);
+  epi.c1(out.hy(6, r6, c6), y6, true);
+  epi.c1(out.hh(6, r6, c6), z6, true);
+  put_ll_epi<Tout>(im, r6, c6, l6, epi);
 }
 
 // ---------------------------------------------------------------------------
 // Synthesis of one 32 x 32 block by one warp (any L <= 6): every load is
 // issued first; no communication between lanes.
 // ---------------------------------------------------------------------------
-template <typename Tin, typename Tout, int L>
-__device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t x0, int lane) {
+template <typename Tin, typename Tout, int L, typename Epi = EpiStore>
+__device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t x0, int lane,
+                                             Epi&& epi = Epi()) {
   using A = typename AccT<Tin>::type;
   static_assert(L >= 1 && L <= 6, "one warp undoes 1..6 levels");
   const int tx = lane & 3, ty = lane >> 2;
@@ -316,8 +346,8 @@ __device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t
     for (int c = 0; c < 4; ++c)
       inv_quad(ll1[rp][c], d1x[rp][c], d1y[rp][c], d1z[rp][c], o0[2 * c], o0[2 * c + 1],
                o1[2 * c], o1[2 * c + 1]);
-    store8(dst + (2 * rp) * im.d_rs, o0);
-    store8(dst + (2 * rp + 1) * im.d_rs, o1);
+    epi.px8(dst + (2 * rp) * im.d_rs, o0);
+    epi.px8(dst + (2 * rp + 1) * im.d_rs, o1);
   }
 }
 
