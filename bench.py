@@ -531,12 +531,12 @@ def grad_form(api, synth, dev):
     ms_rt = time_ms(lambda: (rt.dwt(), rt.idwt()), 50)
     peaks = measured_peaks()
     hbm = (peaks or {}).get("hbm_gbs") or 6800.0
-    gbs = 44.0 * px / (ms_graph * 1e-3) / 1e9
+    gbs = 12.0 * px / (ms_graph * 1e-3) / 1e9
     return {"workload": f"{B}x{C}x{H}x{W} fp32, {L} levels, soft threshold {t}, L1 weight {lam}",
             "fused_graph_ms": round(ms_graph, 4),
             "fused_graph_gsamples_s": round(px / (ms_graph * 1e-3) / 1e9, 2),
             "fused_hbm_gbs": round(gbs, 1), "fused_frac_of_hbm": round(gbs / hbm, 4),
-            "fused_algorithmic_bytes_per_px": 44,
+            "fused_algorithmic_bytes_per_px": 12,
             "fused_autograd_ms": round(ms_fused, 4),
             "unfused_autograd_ms": round(ms_unfused, 4),
             "plain_fp32_dwt_idwt_ms": round(ms_rt, 4),

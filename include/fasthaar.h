@@ -252,23 +252,25 @@ int haar_sq_diff_backward(const haar_desc *a, const haar_desc *b, const haar_des
                           const haar_desc *g_b, double scale, const void *g,
                           void *cuda_stream);
 
-/* The loss, fused into two transform launches plus a one-thread finisher:
- * writes s and the residual r = xr - x, and the loss value to `loss` (device
- * scalar of the dtype).  acc2: device scratch of 2 doubles, zero on entry and
- * left zero on return.  Sides multiples of 32, 1 <= levels <= 6, arrays
- * 16-byte aligned (else HAAR_ESHAPE / HAAR_EINVAL). */
-int haar_denoise_forward(const haar_desc *x, const haar_desc *s, const haar_desc *r, int levels,
-                         double threshold, double l1_weight, double *acc2, void *loss,
-                         void *cuda_stream);
+/* The loss, fused into one launch plus a one-thread finisher, reading x only.
+ * W is orthonormal, so the residual is r = W^T s - x = -W^T clamp(c, -t, t):
+ * each warp takes its 32 x 32 block through the analysis, maps the
+ * coefficients, and runs the synthesis back in registers; nothing but the
+ * loss is written (to `loss`, a device scalar of the dtype).  acc2: device
+ * scratch of 2 doubles, zero on entry and left zero on return.  Sides
+ * multiples of 32, 1 <= levels <= 5, arrays 16-byte aligned (else
+ * HAAR_ESHAPE / HAAR_EINVAL). */
+int haar_denoise_forward(const haar_desc *x, int levels, double threshold, double l1_weight,
+                         double *acc2, void *loss, void *cuda_stream);
 
-/* Gradient of the fused loss with respect to x, from the saved s and r and
- * the upstream gradient g_loss (device scalar of the dtype, NULL meaning 1):
- *   g_c = (2g/n W r + l1_weight g / n_d sign(s) [detail]) [s != 0]
- *   g_x = W^T g_c - 2g/n r
- * in two transform launches; g_c is caller scratch of x's shape. */
-int haar_denoise_backward(const haar_desc *r, const haar_desc *s, const haar_desc *g_c,
-                          const haar_desc *g_x, int levels, double l1_weight,
-                          const void *g_loss, void *cuda_stream);
+/* Gradient of that loss with respect to x, recomputed from x alone, times
+ * the upstream gradient g (device scalar of the dtype, NULL meaning 1):
+ *   g_x = W^T q,  q = [|c| > t] * (l1_weight g / n_d) * sign(c) * [detail]
+ *                   + [|c| <= t] * (2 g / n) * c,         c = W x
+ * (n pixels, n_d detail coefficients), in one launch reading x and writing
+ * g_x.  Same shape rules as haar_denoise_forward; x and g_x must not overlap. */
+int haar_denoise_backward(const haar_desc *x, const haar_desc *g_x, int levels, double threshold,
+                          double l1_weight, const void *g_loss, void *cuda_stream);
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *haar_status_string(int status);

@@ -105,9 +105,9 @@ SIGNATURES = {
     "haar_soft_threshold_backward": (ctypes.c_int, [_DP, _DP, _DP, ctypes.c_int,
                                                     ctypes.c_double, _P, _P]),
     "haar_sq_diff_backward": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_double, _P, _P]),
-    "haar_denoise_forward": (ctypes.c_int, [_DP, _DP, _DP, ctypes.c_int, ctypes.c_double,
+    "haar_denoise_forward": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, _P, _P, _P]),
-    "haar_denoise_backward": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_int,
+    "haar_denoise_backward": (ctypes.c_int, [_DP, _DP, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, _P, _P]),
 }
 

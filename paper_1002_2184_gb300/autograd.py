@@ -8,9 +8,10 @@ Every forward and backward below runs in libfasthaar's kernels.
 Two forms of the loss
     c = W x,  s = soft(c, t),  xr = W^T s,
     loss = mean((xr - x)^2) + lam * mean(|s| over detail coefficients):
-  * ``denoise_loss``: fused -- two transform launches forward (the soft
-    threshold, the L1 sum and the residual are transform epilogues) and two
-    backward;
+  * ``denoise_loss``: fused -- because W W^T = I the residual is
+    xr - x = -W^T clamp(c, -t, t) and the gradient is W^T q with q a
+    per-coefficient map of c, so the forward and the backward are one launch
+    each that read x only (4 and 8 bytes per pixel);
   * ``denoise_loss_unfused``: composed from DWT2d, SoftThresholdL1, IDWT2d
     and MSE, each a separate launch (autograd adds the two gradient
     contributions to x and the loss terms with torch's own elementwise ops).
@@ -150,35 +151,33 @@ class MSE(torch.autograd.Function):
 
 
 class DenoiseLoss(torch.autograd.Function):
-    """The fused loss (haar_denoise_forward / haar_denoise_backward)."""
+    """The fused loss (haar_denoise_forward / haar_denoise_backward): both
+    directions read x only and recompute the transform, so nothing but x is
+    kept for the backward pass."""
 
     @staticmethod
     def forward(ctx, x, levels: int, t: float, lam: float):
         lib = _lib.load()
         x = _contig(x)
-        s = torch.empty_like(x)
-        r = torch.empty_like(x)
         acc = torch.zeros(2, dtype=torch.float64, device=x.device)
         loss = torch.empty((), dtype=x.dtype, device=x.device)
-        _lib.check(lib.haar_denoise_forward(
-            ctypes.byref(api.describe(x)), ctypes.byref(api.describe(s)),
-            ctypes.byref(api.describe(r)), levels, float(t), float(lam), acc.data_ptr(),
-            loss.data_ptr(), _stream(x)), "haar_denoise_forward")
-        ctx.levels, ctx.lam = levels, float(lam)
-        ctx.save_for_backward(s, r)
+        _lib.check(lib.haar_denoise_forward(ctypes.byref(api.describe(x)), levels, float(t),
+                                            float(lam), acc.data_ptr(), loss.data_ptr(),
+                                            _stream(x)), "haar_denoise_forward")
+        ctx.levels, ctx.t, ctx.lam = levels, float(t), float(lam)
+        ctx.save_for_backward(x)
         return loss
 
     @staticmethod
     def backward(ctx, g):
         lib = _lib.load()
-        s, r = ctx.saved_tensors
-        g_c = torch.empty_like(r)
-        g_x = torch.empty_like(r)
-        gg = _contig(g.to(r.dtype).reshape(1))
-        _lib.check(lib.haar_denoise_backward(
-            ctypes.byref(api.describe(r)), ctypes.byref(api.describe(s)),
-            ctypes.byref(api.describe(g_c)), ctypes.byref(api.describe(g_x)), ctx.levels,
-            ctx.lam, gg.data_ptr(), _stream(r)), "haar_denoise_backward")
+        (x,) = ctx.saved_tensors
+        g_x = torch.empty_like(x)
+        gg = _contig(g.to(x.dtype).reshape(1))
+        _lib.check(lib.haar_denoise_backward(ctypes.byref(api.describe(x)),
+                                             ctypes.byref(api.describe(g_x)), ctx.levels,
+                                             ctx.t, ctx.lam, gg.data_ptr(), _stream(x)),
+                   "haar_denoise_backward")
         return g_x, None, None, None
 
 
@@ -222,28 +221,23 @@ class DenoisePlan:
         if not x.is_contiguous():
             raise ValueError("x must be contiguous")
         self.x, self.levels, self.t, self.lam = x, int(levels), float(t), float(lam)
-        self.s = torch.empty_like(x)
-        self.r = torch.empty_like(x)
-        self.g_c = torch.empty_like(x)
         self.grad = torch.empty_like(x)
         self.acc = torch.zeros(2, dtype=torch.float64, device=x.device)
         self.loss = torch.empty((), dtype=x.dtype, device=x.device)
-        self._d = {k: api.describe(getattr(self, k)) for k in ("x", "s", "r", "g_c", "grad")}
-        self._p = {k: ctypes.byref(v) for k, v in self._d.items()}
+        self._dx, self._dg = api.describe(x), api.describe(self.grad)
+        self._px, self._pg = ctypes.byref(self._dx), ctypes.byref(self._dg)
 
     def forward(self, stream=None) -> torch.Tensor:
         st = _stream(self.x) if stream is None else getattr(stream, "cuda_stream", stream)
-        rc = self.lib.haar_denoise_forward(self._p["x"], self._p["s"], self._p["r"], self.levels,
-                                           self.t, self.lam, self.acc.data_ptr(),
-                                           self.loss.data_ptr(), st)
+        rc = self.lib.haar_denoise_forward(self._px, self.levels, self.t, self.lam,
+                                           self.acc.data_ptr(), self.loss.data_ptr(), st)
         if rc:
             _lib.check(rc, "haar_denoise_forward")
         return self.loss
 
     def backward(self, g: torch.Tensor = None, stream=None) -> torch.Tensor:
         st = _stream(self.x) if stream is None else getattr(stream, "cuda_stream", stream)
-        rc = self.lib.haar_denoise_backward(self._p["r"], self._p["s"], self._p["g_c"],
-                                            self._p["grad"], self.levels, self.lam,
+        rc = self.lib.haar_denoise_backward(self._px, self._pg, self.levels, self.t, self.lam,
                                             g.data_ptr() if g is not None else None, st)
         if rc:
             _lib.check(rc, "haar_denoise_backward")

@@ -23,6 +23,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   return v;
 }
+// Sum over the block of one value per thread, added once into *out: warp
+// shuffles, then one shared-memory slot per warp, then one atomic per block
+// (atomics from every warp to one address would serialise).  Every thread of
+// the block must call it.
+__device__ __forceinline__ void block_sum_to(double v, double* out) {
+  __shared__ double part[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = lane < nw ? part[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) atomicAdd(out, t);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
@@ -136,113 +155,161 @@ __global__ void __launch_bounds__(256) k_sqdiff_bwd(const T* __restrict__ a,
 }
 
 // ---------------------------------------------------------------------------
-// Fused loss: epilogues plugged into the warp-block transforms.
+// Fused loss by recomputation.
+//
+// W is orthonormal (W W^T = I), so with c = W x and s = soft(c, t):
+//   r = W^T s - x = W^T (s - c) = -W^T clamp(c, -t, t)
+//   d loss / d x  = W^T q,   q = [|c| > t] * lam' * sign(c) * [detail]
+//                              + [|c| <= t] * (2 g / n) * c,   lam' = lam g / n_d
+// (g: upstream gradient; n pixels, n_d detail coefficients).  Neither s nor
+// r has to be stored: the forward reads x and produces only the loss sums,
+// the backward reads x and writes the gradient.  Each is one kernel in which
+// a warp takes its 32 x 32 block through the analysis (registers and
+// shuffles, as dwt_block32), maps every coefficient in place, and runs the
+// synthesis back in registers (each lane holds every coarse coefficient on
+// its own path after the shuffles).
 // ---------------------------------------------------------------------------
-// Forward analysis: store s = soft(c, t); accumulate |s| over details.
-template <typename T>
-struct EpiSoft {
-  T t;
-  T l1;
-  const T* base;
-  __device__ __forceinline__ T f(T v, bool d) {
-    const T s = soft(v, t);
-    if (d) l1 += fabs(s);
-    return s;
-  }
-  __device__ __forceinline__ void c4(T* p, const T v[4], bool d) {
-    T o[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[k] = f(v[k], d);
-    store4(p, o);
-  }
-  __device__ __forceinline__ void c2(T* p, const T v[2], bool d) {
-    T o[2] = {f(v[0], d), f(v[1], d)};
-    store2(p, o);
-  }
-  __device__ __forceinline__ void c1(T* p, T v, bool d) { *p = f(v, d); }
-  __device__ __forceinline__ void px8(T* p, const T v[8]) { store8(p, v); }
+template <typename T, int L>
+struct WarpCoefs {
+  T x1[2][4], y1[2][4], z1[2][4];  // level-1 details (Hx, Hy, HH) of the lane
+  T x2[2], y2[2], z2[2];           // level-2 details
+  T xl[6], yl[6], zl[6];           // levels 3..5 (shared with the lane's group)
+  T ll1[2][4], ll2[2], ll;         // low band: LL1 (L = 1), LL2 (L = 2), LL_L (L >= 3)
 };
 
-// Forward synthesis: store r = xr - x; accumulate r^2.
-template <typename T>
-struct EpiResid {
-  const T* x;     // same layout as the output
-  const T* base;  // output base the offsets are taken from
-  T sq;
-  __device__ __forceinline__ void px8(T* p, const T v[8]) {
-    T xv[8], r[8];
-    load8(x + (p - base), xv);
+// Analysis of the block into registers (same operations as dwt_block32).
+template <typename T, int L>
+__device__ __forceinline__ void warp_analysis(const T* src, int64_t rs, int lane, WarpCoefs<T, L>& k) {
+  const int tx = lane & 3, ty = lane >> 2;
+  T v[4][8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      r[k] = v[k] - xv[k];
-      sq += r[k] * r[k];
+  for (int r = 0; r < 4; ++r) load8(src + r * rs, v[r]);
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      fwd_quad(v[2 * rp][2 * c], v[2 * rp][2 * c + 1], v[2 * rp + 1][2 * c],
+               v[2 * rp + 1][2 * c + 1], k.ll1[rp][c], k.x1[rp][c], k.y1[rp][c], k.z1[rp][c]);
+  if constexpr (L >= 2) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      fwd_quad(k.ll1[0][2 * c], k.ll1[0][2 * c + 1], k.ll1[1][2 * c], k.ll1[1][2 * c + 1],
+               k.ll2[c], k.x2[c], k.y2[c], k.z2[c]);
+  }
+  if constexpr (L >= 3) {
+    T l3;
+    vpair(k.ll2[0] + k.ll2[1], k.ll2[1] - k.ll2[0], (ty & 1) != 0, 4, l3, k.xl[3], k.yl[3],
+          k.zl[3]);
+    k.ll = l3;
+  }
+  if constexpr (L >= 4) {
+    T lo, hi, l4;
+    hpair(k.ll, (tx & 1) != 0, 1, lo, hi);
+    vpair(lo, hi, ((ty >> 1) & 1) != 0, 8, l4, k.xl[4], k.yl[4], k.zl[4]);
+    k.ll = l4;
+  }
+  if constexpr (L >= 5) {
+    T lo, hi, l5;
+    hpair(k.ll, (tx & 2) != 0, 2, lo, hi);
+    vpair(lo, hi, (ty & 4) != 0, 16, l5, k.xl[5], k.yl[5], k.zl[5]);
+    k.ll = l5;
+  }
+}
+
+// Applies op(value, detail, owner) to every coefficient the lane holds;
+// `owner` is true for exactly one copy of each coefficient in the warp (the
+// coarse levels are duplicated across lane groups), so sums count each once.
+template <typename T, int L, typename Op>
+__device__ __forceinline__ void warp_map(int lane, WarpCoefs<T, L>& k, Op& op) {
+  const int tx = lane & 3, ty = lane >> 2;
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      k.x1[rp][c] = op(k.x1[rp][c], true, true);
+      k.y1[rp][c] = op(k.y1[rp][c], true, true);
+      k.z1[rp][c] = op(k.z1[rp][c], true, true);
+      if constexpr (L == 1) k.ll1[rp][c] = op(k.ll1[rp][c], false, true);
     }
-    store8(p, r);
+  if constexpr (L >= 2) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      k.x2[c] = op(k.x2[c], true, true);
+      k.y2[c] = op(k.y2[c], true, true);
+      k.z2[c] = op(k.z2[c], true, true);
+      if constexpr (L == 2) k.ll2[c] = op(k.ll2[c], false, true);
+    }
   }
-  template <typename A>
-  __device__ __forceinline__ void c4(T*, const A*, bool) {}
-  template <typename A>
-  __device__ __forceinline__ void c2(T*, const A*, bool) {}
-  template <typename A>
-  __device__ __forceinline__ void c1(T*, A, bool) {}
+  const bool own[6] = {false, false, false, (ty & 1) == 0, (ty & 3) == 0 && (tx & 1) == 0,
+                       lane == 0};
+#pragma unroll
+  for (int l = 3; l <= L; ++l) {
+    k.xl[l] = op(k.xl[l], true, own[l]);
+    k.yl[l] = op(k.yl[l], true, own[l]);
+    k.zl[l] = op(k.zl[l], true, own[l]);
+  }
+  if constexpr (L >= 3) k.ll = op(k.ll, false, own[L]);
+}
+
+// Synthesis of the (mapped) coefficients back to the lane's 4 x 8 pixels.
+template <typename T, int L>
+__device__ __forceinline__ void warp_synthesis(int lane, int64_t py, int64_t px,
+                                               WarpCoefs<T, L>& k, T o[4][8]) {
+  (void)lane;
+  if constexpr (L >= 3) {
+    T v = k.ll;
+#pragma unroll
+    for (int l = L; l >= 4; --l)
+      v = inv_child(v, k.xl[l], k.yl[l], k.zl[l], (int)((py >> (l - 1)) & 1),
+                    (int)((px >> (l - 1)) & 1));
+    const int qy = (int)((py >> 2) & 1);
+    k.ll2[0] = inv_child(v, k.xl[3], k.yl[3], k.zl[3], qy, 0);
+    k.ll2[1] = inv_child(v, k.xl[3], k.yl[3], k.zl[3], qy, 1);
+  }
+  if constexpr (L >= 2) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      inv_quad(k.ll2[c], k.x2[c], k.y2[c], k.z2[c], k.ll1[0][2 * c], k.ll1[0][2 * c + 1],
+               k.ll1[1][2 * c], k.ll1[1][2 * c + 1]);
+  }
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      inv_quad(k.ll1[rp][c], k.x1[rp][c], k.y1[rp][c], k.z1[rp][c], o[2 * rp][2 * c],
+               o[2 * rp][2 * c + 1], o[2 * rp + 1][2 * c], o[2 * rp + 1][2 * c + 1]);
+}
+
+// Forward map: c -> -clamp(c, -t, t) = soft(c) - c; sums |soft(c)| over details.
+template <typename T>
+struct OpResidual {
+  T t, l1;
+  __device__ __forceinline__ T operator()(T c, bool detail, bool owner) {
+    const T a = fabs(c) - t;
+    if (detail && owner && a > T(0)) l1 += a;
+    return a > T(0) ? copysign(t, -c) : -c;
+  }
 };
 
-// Backward analysis of r: g_c = (scale * W r + lam * sign(s) * detail) * [s != 0].
+// Backward map: c -> [|c| > t] lam sign(c) [detail] + [|c| <= t] scale c.
 template <typename T>
-struct EpiGradC {
-  const T* s;
-  const T* base;
-  T scale, lam;
-  __device__ __forceinline__ T f(T v, T sv, bool d) {
-    if (sv == T(0)) return T(0);
-    T g = scale * v;
-    if (d) g += sv > T(0) ? lam : -lam;
-    return g;
+struct OpGradient {
+  T t, scale, lam;
+  __device__ __forceinline__ T operator()(T c, bool detail, bool) {
+    if (fabs(c) > t) return detail ? copysign(lam, c) : T(0);
+    return scale * c;
   }
-  __device__ __forceinline__ void c4(T* p, const T v[4], bool d) {
-    T sv[4], o[4];
-    load4(s + (p - base), sv);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[k] = f(v[k], sv[k], d);
-    store4(p, o);
-  }
-  __device__ __forceinline__ void c2(T* p, const T v[2], bool d) {
-    T sv[2];
-    load2(s + (p - base), sv);
-    T o[2] = {f(v[0], sv[0], d), f(v[1], sv[1], d)};
-    store2(p, o);
-  }
-  __device__ __forceinline__ void c1(T* p, T v, bool d) { *p = f(v, ld_scalar(s + (p - base)), d); }
-  __device__ __forceinline__ void px8(T* p, const T v[8]) { store8(p, v); }
-};
-
-// Backward synthesis: g_x = W^T g_c - scale * r.
-template <typename T>
-struct EpiGradX {
-  const T* r;
-  const T* base;
-  T scale;
-  __device__ __forceinline__ void px8(T* p, const T v[8]) {
-    T rv[8], o[8];
-    load8(r + (p - base), rv);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = v[k] - scale * rv[k];
-    store8(p, o);
-  }
-  template <typename A>
-  __device__ __forceinline__ void c4(T*, const A*, bool) {}
-  template <typename A>
-  __device__ __forceinline__ void c2(T*, const A*, bool) {}
-  template <typename A>
-  __device__ __forceinline__ void c1(T*, A, bool) {}
 };
 
 struct DenoiseArgs {
-  Pass p;             // src, dst of this launch; ll = dst; batch, h, w, levels
-  const void* aux;    // second input read at the output's positions (x, s or r)
-  double* acc;        // FP64 accumulators: [0] = sum |s_detail|, [1] = sum r^2
-  const void* g;      // upstream gradient of the loss (device scalar) or null
-  double k1, k2;      // per-launch constants (see the launchers)
+  const void* x;
+  void* gx;          // backward output (same layout as x)
+  int64_t batch, h, w;
+  int64_t tiles_x, tiles_y, ntiles;
+  double* acc;       // forward sums: [0] = sum |s_detail|, [1] = sum r^2
+  const void* g;     // upstream gradient (device scalar) or null (= 1)
+  double t, k_scale, k_lam;  // threshold; 2/n; lam/n_d
+  int levels;        // 1..5
 };
 
 template <typename T>
@@ -250,85 +317,66 @@ __device__ __forceinline__ T load_g(const void* g) {
   return g ? *static_cast<const T*>(g) : T(1);
 }
 
-// Tile decode shared by the four fused kernels (same geometry as the
-// strided-batch fast kernels).
-struct TileXY {
-  int64_t b, cy, cx, y0, x0;
-};
-template <int WR, int WC>
-__device__ __forceinline__ TileXY tile_xy(const Pass& p, int warp) {
-  TileXY t;
-  const int64_t per = p.tiles_x * p.tiles_y;
+// Block of 8 warps side by side: 32 x 256 pixels of one image.
+__device__ __forceinline__ bool dn_block(const DenoiseArgs& a, int64_t& off, int64_t& py,
+                                         int64_t& px) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t per = a.tiles_x * a.tiles_y;
   const int64_t bt = blockIdx.x;
-  t.b = bt / per;
-  const int64_t rr = bt - t.b * per;
-  t.cy = rr / p.tiles_x;
-  t.cx = rr - t.cy * p.tiles_x;
-  t.y0 = t.cy * (32 * WR) + (warp / WC) * 32;
-  t.x0 = t.cx * (32 * WC) + (warp % WC) * 32;
-  return t;
+  const int64_t b = bt / per, rr = bt - b * per;
+  const int64_t cy = rr / a.tiles_x, cx = rr - cy * a.tiles_x;
+  const int64_t y0 = cy * 32, x0 = cx * 256 + warp * 32;
+  py = y0 + 4 * (lane >> 2);
+  px = x0 + 8 * (lane & 3);
+  off = b * a.h * a.w;
+  return y0 < a.h && x0 < a.w;
 }
 
-template <typename T, int L, typename Epi>
-__device__ __forceinline__ void fused_analysis(const Pass& p, Epi& epi) {
-  constexpr int WR = (L == 6) ? 2 : 1;
-  constexpr int WC = 8 / WR;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TileXY t = tile_xy<WR, WC>(p, warp);
-  const Img2 im = pass_image<T, T>(p, t.b);
-  // offsets into the second array are taken from the batch base (the
-  // arrays share one contiguous layout)
-  epi.base = static_cast<const T*>(p.dst);
-  T l5 = T(0);
-  if (t.y0 < p.h && t.x0 < p.w) l5 = dwt_block32<T, T, L>(im, t.y0, t.x0, lane, epi);
-  if constexpr (L == 6) {
-    __shared__ T s5[WR][WC];
-    if (lane == 0) s5[warp / WC][warp % WC] = l5;
-    __syncthreads();
-    if (threadIdx.x < WC / 2) {
-      const int j = threadIdx.x;
-      const int64_t by0 = t.cy * 64, bx0 = t.cx * 128 + 64 * j;
-      if (by0 < p.h && bx0 < p.w)
-        dwt_level6<T>(im, s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j], s5[1][2 * j + 1], by0,
-                      bx0, epi);
-    }
+template <typename T, int L>
+__global__ void __launch_bounds__(256) k_denoise_loss(const DenoiseArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  int64_t off, py, px;
+  OpResidual<T> op{(T)a.t, T(0)};
+  T sq = T(0);
+  if (dn_block(a, off, py, px)) {  // warps outside the image contribute zeros
+    const T* x = static_cast<const T*>(a.x) + off;
+    WarpCoefs<T, L> k;
+    warp_analysis<T, L>(x + py * a.w + px, a.w, lane, k);
+    warp_map<T, L>(lane, k, op);
+    T r[4][8];
+    warp_synthesis<T, L>(lane, py, px, k, r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sq += r[i][j] * r[i][j];
   }
+  block_sum_to((double)op.l1, a.acc);
+  block_sum_to((double)sq, a.acc + 1);
 }
 
-template <typename T, int L, typename Epi>
-__device__ __forceinline__ bool fused_synthesis(const Pass& p, Epi& epi) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TileXY t = tile_xy<1, 8>(p, warp);
-  if (t.y0 >= p.h || t.x0 >= p.w) return false;
-  const Img2 im = pass_image<T, T>(p, t.b);
-  epi.base = static_cast<const T*>(p.dst);
-  idwt_block32<T, T, L>(im, t.y0, t.x0, lane, epi);
-  return true;
-}
-
-// Forward, launch 1: x -> s.  k1 = threshold.
 template <typename T, int L>
-__global__ void __launch_bounds__(256) k_denoise_a(const DenoiseArgs a) {
+__global__ void __launch_bounds__(256) k_denoise_grad(const DenoiseArgs a) {
   pdl_wait();
   pdl_trigger();
-  EpiSoft<T> epi{(T)a.k1, T(0), nullptr};
-  fused_analysis<T, L>(a.p, epi);
-  const double tot = warp_sum((double)epi.l1);
-  if ((threadIdx.x & 31) == 0) atomicAdd(a.acc, tot);
+  const int lane = threadIdx.x & 31;
+  int64_t off, py, px;
+  if (!dn_block(a, off, py, px)) return;
+  const T g = load_g<T>(a.g);
+  const T* x = static_cast<const T*>(a.x) + off;
+  WarpCoefs<T, L> k;
+  warp_analysis<T, L>(x + py * a.w + px, a.w, lane, k);
+  OpGradient<T> op{(T)a.t, (T)a.k_scale * g, (T)a.k_lam * g};
+  warp_map<T, L>(lane, k, op);
+  T o[4][8];
+  warp_synthesis<T, L>(lane, py, px, k, o);
+  T* gx = static_cast<T*>(a.gx) + off + py * a.w + px;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) store8(gx + i * a.w, o[i]);
 }
 
-// Forward, launch 2: s -> r = IDWT(s) - x.
-template <typename T, int L>
-__global__ void __launch_bounds__(256) k_denoise_b(const DenoiseArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  EpiResid<T> epi{static_cast<const T*>(a.aux), nullptr, T(0)};
-  if (!fused_synthesis<T, L>(a.p, epi)) return;  // whole warp outside the image
-  const double tot = warp_sum((double)epi.sq);
-  if ((threadIdx.x & 31) == 0) atomicAdd(a.acc + 1, tot);
-}
-
-// loss = acc[1] * k1 + acc[0] * k2 (k1 = 1/n, k2 = lambda/n_d); clears acc.
+// loss = acc[1] / n + lam / n_d * acc[0]; clears acc for the next call.
 template <typename T>
 __global__ void k_denoise_finalize(double* acc, T* loss, double k1, double k2) {
   pdl_wait();
@@ -340,54 +388,27 @@ __global__ void k_denoise_finalize(double* acc, T* loss, double k1, double k2) {
   }
 }
 
-// Backward, launch 1: r -> g_c.  k1 = 2/n, k2 = lambda/n_d (times g).
-template <typename T, int L>
-__global__ void __launch_bounds__(256) k_denoise_c(const DenoiseArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  const T g = load_g<T>(a.g);
-  EpiGradC<T> epi{static_cast<const T*>(a.aux), nullptr, (T)a.k1 * g, (T)a.k2 * g};
-  fused_analysis<T, L>(a.p, epi);
-}
-
-// Backward, launch 2: g_c -> g_x = IDWT(g_c) - (2g/n) r.  k1 = 2/n.
-template <typename T, int L>
-__global__ void __launch_bounds__(256) k_denoise_d(const DenoiseArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  const T g = load_g<T>(a.g);
-  EpiGradX<T> epi{static_cast<const T*>(a.aux), nullptr, (T)a.k1 * g};
-  fused_synthesis<T, L>(a.p, epi);
-}
-
 template <typename T>
-cudaError_t denoise_launch(int which, DenoiseArgs a, cudaStream_t s) {
-  const bool ana = (which == 0 || which == 2);
-  const int CH = (ana && a.p.levels == 6) ? 64 : 32, CW = (ana && a.p.levels == 6) ? 128 : 256;
-  a.p.tiles_x = (a.p.w + CW - 1) / CW;
-  a.p.tiles_y = (a.p.h + CH - 1) / CH;
-  a.p.ntiles = a.p.batch * a.p.tiles_x * a.p.tiles_y;
-  if (a.p.ntiles == 0) return cudaSuccess;
-  if (a.p.ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  const unsigned g = (unsigned)a.p.ntiles;
-#define FH_DENOISE_CASE(LV)                                                  \
-  case LV:                                                                   \
-    switch (which) {                                                         \
-      case 0: return launch_pdl(k_denoise_a<T, LV>, g, 256, s, a);          \
-      case 1: return launch_pdl(k_denoise_b<T, LV>, g, 256, s, a);          \
-      case 2: return launch_pdl(k_denoise_c<T, LV>, g, 256, s, a);          \
-      default: return launch_pdl(k_denoise_d<T, LV>, g, 256, s, a);         \
-    }
-  switch (a.p.levels) {
-    FH_DENOISE_CASE(1)
-    FH_DENOISE_CASE(2)
-    FH_DENOISE_CASE(3)
-    FH_DENOISE_CASE(4)
-    FH_DENOISE_CASE(5)
-    FH_DENOISE_CASE(6)
+cudaError_t denoise_launch(bool grad, DenoiseArgs a, cudaStream_t s) {
+  a.tiles_x = (a.w + 255) / 256;
+  a.tiles_y = (a.h + 31) / 32;
+  a.ntiles = a.batch * a.tiles_x * a.tiles_y;
+  if (a.ntiles == 0) return cudaSuccess;
+  if (a.ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned g = (unsigned)a.ntiles;
+#define FH_DN_CASE(LV)                                                                   \
+  case LV:                                                                               \
+    return grad ? launch_pdl(k_denoise_grad<T, LV>, g, 256, s, a)                        \
+                : launch_pdl(k_denoise_loss<T, LV>, g, 256, s, a);
+  switch (a.levels) {
+    FH_DN_CASE(1)
+    FH_DN_CASE(2)
+    FH_DN_CASE(3)
+    FH_DN_CASE(4)
+    FH_DN_CASE(5)
     default: return cudaErrorInvalidValue;
   }
-#undef FH_DENOISE_CASE
+#undef FH_DN_CASE
 }
 
 inline unsigned ew_grid(int64_t n) {
@@ -430,41 +451,18 @@ int check_same(const haar_desc* a, const haar_desc* b) {
 
 int64_t numel(const haar_desc* d) { return d->batch * d->h * d->w; }
 
-// The fused pipeline runs on the warp-block kernels: sides multiples of 32,
-// 1..6 levels, 16-byte aligned contiguous arrays.
+// The fused loss runs on the warp-block kernels: sides multiples of 32,
+// 1..5 levels (one warp per 32 x 32 block), 16-byte aligned contiguous arrays.
 int check_fused(const haar_desc* d, int levels) {
-  if (levels < 1 || levels > 6) return HAAR_EINVAL;
+  if (levels < 1 || levels > 5) return HAAR_EINVAL;
   if (d->h % 32 || d->w % 32) return HAAR_ESHAPE;
   if ((d->h & ((1 << levels) - 1)) || (d->w & ((1 << levels) - 1))) return HAAR_ESHAPE;
   if ((uintptr_t)d->ptr % 16) return HAAR_EINVAL;
   return HAAR_OK;
 }
 
-// One fused launch src -> dst.  The low band of the deepest level lives in
-// the coefficient array: the destination of an analysis, the source of a
-// synthesis.
-Pass make_pass(const haar_desc* src, const haar_desc* dst, int levels, bool synthesis) {
-  Pass p{};
-  p.src = src->ptr;
-  p.s_bs = src->h * src->w;
-  p.s_rs = src->w;
-  p.dst = dst->ptr;
-  p.d_bs = dst->h * dst->w;
-  p.d_rs = dst->w;
-  p.ll = synthesis ? src->ptr : dst->ptr;
-  p.l_bs = p.d_bs;
-  p.l_rs = p.d_rs;
-  p.ll_acc = 0;
-  p.levels = levels;
-  p.batch = src->batch;
-  p.h = src->h;
-  p.w = src->w;
-  return p;
-}
-
-cudaError_t denoise_dispatch(int dtype, int which, const DenoiseArgs& a, cudaStream_t s) {
-  return dtype == HAAR_F64 ? denoise_launch<double>(which, a, s)
-                           : denoise_launch<float>(which, a, s);
+cudaError_t denoise_dispatch(int dtype, bool grad, const DenoiseArgs& a, cudaStream_t s) {
+  return dtype == HAAR_F64 ? denoise_launch<double>(grad, a, s) : denoise_launch<float>(grad, a, s);
 }
 
 }  // namespace
@@ -559,30 +557,25 @@ int haar_sq_diff_backward(const haar_desc* a, const haar_desc* b, const haar_des
                          (const float*)g));
 }
 
-int haar_denoise_forward(const haar_desc* x, const haar_desc* s, const haar_desc* r, int levels,
-                         double threshold, double l1_weight, double* acc2, void* loss,
-                         void* cuda_stream) {
-  int rc = check_same(x, s);
-  if (!rc) rc = check_same(x, r);
+int haar_denoise_forward(const haar_desc* x, int levels, double threshold, double l1_weight,
+                         double* acc2, void* loss, void* cuda_stream) {
+  int rc = check_same(x, x);
   if (rc) return rc;
   if (!acc2 || !loss || !(threshold >= 0.0)) return HAAR_EINVAL;
   const int64_t n = numel(x);
   if (n == 0) return HAAR_OK;
-  if ((rc = check_fused(x, levels)) || (rc = check_fused(s, levels)) ||
-      (rc = check_fused(r, levels)))
-    return rc;
+  if ((rc = check_fused(x, levels))) return rc;
   const cudaStream_t st = (cudaStream_t)cuda_stream;
   const int64_t nd = x->batch * (x->h * x->w - (x->h >> levels) * (x->w >> levels));
   DenoiseArgs a{};
+  a.x = x->ptr;
+  a.batch = x->batch;
+  a.h = x->h;
+  a.w = x->w;
   a.acc = acc2;
-  a.p = make_pass(x, s, levels, false);  // x -> s
-  a.k1 = threshold;
-  cudaError_t e = denoise_dispatch(x->dtype, 0, a, st);
-  if (e == cudaSuccess) {
-    a.p = make_pass(s, r, levels, true);  // s -> r
-    a.aux = x->ptr;
-    e = denoise_dispatch(x->dtype, 1, a, st);
-  }
+  a.t = threshold;
+  a.levels = levels;
+  cudaError_t e = denoise_dispatch(x->dtype, false, a, st);
   if (e == cudaSuccess) {
     const double k1 = 1.0 / (double)n, k2 = nd ? l1_weight / (double)nd : 0.0;
     if (x->dtype == HAAR_F64)
@@ -593,33 +586,30 @@ int haar_denoise_forward(const haar_desc* x, const haar_desc* s, const haar_desc
   return fail(e);
 }
 
-int haar_denoise_backward(const haar_desc* r, const haar_desc* s, const haar_desc* g_c,
-                          const haar_desc* g_x, int levels, double l1_weight, const void* g_loss,
-                          void* cuda_stream) {
-  int rc = check_same(r, s);
-  if (!rc) rc = check_same(r, g_c);
-  if (!rc) rc = check_same(r, g_x);
+int haar_denoise_backward(const haar_desc* x, const haar_desc* g_x, int levels, double threshold,
+                          double l1_weight, const void* g_loss, void* cuda_stream) {
+  int rc = check_same(x, g_x);
   if (rc) return rc;
-  const int64_t n = numel(r);
+  if (!(threshold >= 0.0)) return HAAR_EINVAL;
+  const int64_t n = numel(x);
   if (n == 0) return HAAR_OK;
-  if ((rc = check_fused(r, levels)) || (rc = check_fused(s, levels)) ||
-      (rc = check_fused(g_c, levels)) || (rc = check_fused(g_x, levels)))
-    return rc;
-  const cudaStream_t st = (cudaStream_t)cuda_stream;
-  const int64_t nd = r->batch * (r->h * r->w - (r->h >> levels) * (r->w >> levels));
+  if ((rc = check_fused(x, levels)) || (rc = check_fused(g_x, levels))) return rc;
+  const uintptr_t xl = (uintptr_t)x->ptr, gl = (uintptr_t)g_x->ptr;
+  const uintptr_t bytes = (uintptr_t)n * (uintptr_t)(x->dtype == HAAR_F64 ? 8 : 4);
+  if (xl < gl + bytes && gl < xl + bytes) return HAAR_EALIAS;
+  const int64_t nd = x->batch * (x->h * x->w - (x->h >> levels) * (x->w >> levels));
   DenoiseArgs a{};
+  a.x = x->ptr;
+  a.gx = g_x->ptr;
+  a.batch = x->batch;
+  a.h = x->h;
+  a.w = x->w;
   a.g = g_loss;
-  a.p = make_pass(r, g_c, levels, false);  // r -> g_c
-  a.aux = s->ptr;
-  a.k1 = 2.0 / (double)n;
-  a.k2 = nd ? l1_weight / (double)nd : 0.0;
-  cudaError_t e = denoise_dispatch(r->dtype, 2, a, st);
-  if (e == cudaSuccess) {
-    a.p = make_pass(g_c, g_x, levels, true);  // g_c -> g_x
-    a.aux = r->ptr;
-    e = denoise_dispatch(r->dtype, 3, a, st);
-  }
-  return fail(e);
+  a.t = threshold;
+  a.k_scale = 2.0 / (double)n;
+  a.k_lam = nd ? l1_weight / (double)nd : 0.0;
+  a.levels = levels;
+  return fail(denoise_dispatch(x->dtype, true, a, (cudaStream_t)cuda_stream));
 }
 
 }  // extern "C"

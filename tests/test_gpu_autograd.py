@@ -142,3 +142,56 @@ def test_parseval_at_full_size_fp64_reduction():
     assert lib.haar_norms_f64(x.data_ptr(), None, 0, x.numel(), ex.data_ptr(), st) == 0
     assert lib.haar_norms_f64(c.data_ptr(), None, 0, c.numel(), ec.data_ptr(), st) == 0
     assert abs(float(ec[0]) / float(ex[0]) - 1.0) <= 1e-6
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3, 4, 5])
+def test_fused_every_level_count_fp64(levels):
+    """Every compiled level count of the fused loss, in FP64, against the
+    oracle's loss and closed-form gradient (tight tolerance)."""
+    x = images((2, 2, 64, 96), 9, torch.float64).requires_grad_(True)
+    loss = ad.denoise_loss(x, levels, 0.05, 1e-3)
+    loss.backward()
+    xn = x.detach().cpu().numpy()
+    ref_loss, _, _ = oracle.denoise_loss(xn, levels, 0.05, 1e-3)
+    ref_g = oracle.denoise_loss_grad(xn, levels, 0.05, 1e-3)
+    assert abs(float(loss) - ref_loss) <= 1e-12 * abs(ref_loss)
+    assert oracle.rel_l2(x.grad.cpu().numpy(), ref_g) <= 1e-11
+
+
+def test_fused_rejects_unsupported_shapes():
+    lib = _lib.load()
+    acc = torch.zeros(2, dtype=torch.float64, device=DEV)
+    loss = torch.empty((), device=DEV)
+    x = torch.zeros(1, 64, 64, device=DEV)
+    d = api.describe(x)
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.haar_denoise_forward(ctypes.byref(d), 6, 0.05, 1e-3, acc.data_ptr(),
+                                    loss.data_ptr(), st) == _lib.HAAR_EINVAL
+    y = torch.zeros(1, 48, 64, device=DEV)
+    assert lib.haar_denoise_forward(ctypes.byref(api.describe(y)), 3, 0.05, 1e-3, acc.data_ptr(),
+                                    loss.data_ptr(), st) == _lib.HAAR_ESHAPE
+    g = torch.empty_like(x)
+    assert lib.haar_denoise_backward(ctypes.byref(d), ctypes.byref(d), 3, 0.05, 1e-3, None,
+                                     st) == _lib.HAAR_EALIAS
+    assert lib.haar_denoise_backward(ctypes.byref(d), ctypes.byref(api.describe(g)), 3, 0.05,
+                                     1e-3, None, st) == _lib.HAAR_OK
+
+
+def test_denoise_plan_in_a_graph_matches_autograd():
+    x = images((2, 3, 128, 128), 6, torch.float32)
+    plan = ad.DenoisePlan(x, 3, 0.05, 1e-3)
+    plan.forward()
+    plan.backward()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.forward()
+        plan.backward()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    xr = x.clone().requires_grad_(True)
+    loss = ad.denoise_loss(xr, 3, 0.05, 1e-3)
+    loss.backward()
+    assert abs(float(plan.loss) - float(loss)) <= 1e-6 * abs(float(loss))
+    assert torch.allclose(plan.grad, xr.grad, rtol=0, atol=0)
