@@ -216,6 +216,24 @@ int haar_ragged_status(const haar_ragged_plan *plan, void *workspace, int *statu
 int haar_ragged_plan_destroy(haar_ragged_plan *plan);
 
 /* ------------------------------------------------------------------------
+ * Wavelet shrinkage in one pass (the paper's denoising use case for
+ * biosignals and medical images, Section VI; the shrinkage rule is the
+ * standard one, not the paper's): y = W^T shrink(W x), where every detail
+ * coefficient d becomes sign(d) max(|d| - t, 0) (soft) or d [|d| > t]
+ * (hard) and the low band is kept.  The coefficients never leave the
+ * registers of the warp that owns the block: 1D, 256 samples per warp and up
+ * to 8 levels (length a multiple of 256); 2D, 32 x 32 pixels per warp and up
+ * to 5 levels (sides multiples of 32).  x and y: same shape, F32 or F64,
+ * 16-byte aligned rows, not overlapping.
+ * ---------------------------------------------------------------------- */
+enum { HAAR_THRESH_SOFT = 0, HAAR_THRESH_HARD = 1 };
+
+int haar_denoise_1d(const haar_desc *x, const haar_desc *y, int levels, double threshold,
+                    int mode, void *cuda_stream);
+int haar_denoise_2d(const haar_desc *x, const haar_desc *y, int levels, double threshold,
+                    int mode, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Verification reductions and a differentiable denoising loss built on the
  * transform (the paper has neither: they serve checking and training).  The
  * loss, for a contiguous batch of h x w images with an L-level transform W:

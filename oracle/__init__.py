@@ -244,6 +244,35 @@ def denoise_loss_grad(x, levels: int, t: float, lam: float) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Wavelet shrinkage (denoising): threshold every detail coefficient, keep the
+# low band, transform back.
+# --------------------------------------------------------------------------
+
+def shrink(d, t: float, hard: bool = False) -> np.ndarray:
+    d = _f64(d)
+    if hard:
+        return np.where(np.abs(d) > t, d, 0.0)
+    return np.sign(d) * np.maximum(np.abs(d) - t, 0.0)
+
+
+def denoise1d(x, levels: int, t: float, hard: bool = False) -> np.ndarray:
+    x = _f64(x)
+    c = dwt1d(x, levels)
+    mask = np.broadcast_to(detail_mask_1d(x.shape[-1], levels), c.shape)
+    c = np.where(mask, shrink(c, t, hard), c)
+    return idwt1d(c, levels)
+
+
+def denoise2d(x, levels: int, t: float, hard: bool = False) -> np.ndarray:
+    x = _f64(x)
+    h, w = x.shape[-2:]
+    c = dwt2d(x, levels)
+    mask = np.broadcast_to(detail_mask_2d(h, w, levels), c.shape)
+    c = np.where(mask, shrink(c, t, hard), c)
+    return idwt2d(c, levels)
+
+
+# --------------------------------------------------------------------------
 # Error measures reported next to every result.
 # --------------------------------------------------------------------------
 
@@ -263,5 +292,5 @@ __all__ = [
     "lib", "analysis_1d", "synthesis_1d", "polyphase_analysis_1d",
     "polyphase_synthesis_1d", "dwt1d", "idwt1d", "dwt2d", "idwt2d",
     "detail_mask_1d", "detail_mask_2d", "soft_threshold", "denoise_loss",
-    "denoise_loss_grad", "rel_l2", "max_abs",
+    "denoise_loss_grad", "shrink", "denoise1d", "denoise2d", "rel_l2", "max_abs",
 ]

@@ -26,6 +26,9 @@ HAAR_EQUEUE = -8
 # Storage types.
 HAAR_F32, HAAR_BF16, HAAR_F16, HAAR_U8, HAAR_F64 = 0, 1, 2, 3, 4
 
+# Shrinkage rules of haar_denoise_1d / haar_denoise_2d.
+HAAR_THRESH_SOFT, HAAR_THRESH_HARD = 0, 1
+
 # Ragged work-unit shapes.
 HAAR_UNIT_64x128, HAAR_UNIT_32x256 = 0, 1
 
@@ -105,6 +108,10 @@ SIGNATURES = {
     "haar_soft_threshold_backward": (ctypes.c_int, [_DP, _DP, _DP, ctypes.c_int,
                                                     ctypes.c_double, _P, _P]),
     "haar_sq_diff_backward": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_double, _P, _P]),
+    "haar_denoise_1d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       _P]),
+    "haar_denoise_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       _P]),
     "haar_denoise_forward": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, _P, _P, _P]),
     "haar_denoise_backward": (ctypes.c_int, [_DP, _DP, ctypes.c_int, ctypes.c_double,

@@ -279,3 +279,32 @@ class RaggedPlan:
         if h is not None and h.value and _lib._LIB is not None:
             _lib._LIB.haar_ragged_plan_destroy(h)
             self._h = None
+
+
+def denoise1d(x: torch.Tensor, levels: int, threshold: float, hard: bool = False,
+              out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """One-pass wavelet shrinkage of every row of (..., n): analysis, soft
+    (or hard) thresholding of the detail coefficients, synthesis."""
+    out = _out_like(x, x.dtype, out)
+    lib = _lib.load()
+    with torch.cuda.device(x.device):
+        rc = lib.haar_denoise_1d(ctypes.byref(describe(x, True)), ctypes.byref(describe(out, True)),
+                                 levels, float(threshold),
+                                 _lib.HAAR_THRESH_HARD if hard else _lib.HAAR_THRESH_SOFT,
+                                 _stream(x))
+    _lib.check(rc, "haar_denoise_1d")
+    return out
+
+
+def denoise2d(x: torch.Tensor, levels: int, threshold: float, hard: bool = False,
+              out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """One-pass wavelet shrinkage of every image of (..., h, w)."""
+    out = _out_like(x, x.dtype, out)
+    lib = _lib.load()
+    with torch.cuda.device(x.device):
+        rc = lib.haar_denoise_2d(ctypes.byref(describe(x)), ctypes.byref(describe(out)), levels,
+                                 float(threshold),
+                                 _lib.HAAR_THRESH_HARD if hard else _lib.HAAR_THRESH_SOFT,
+                                 _stream(x))
+    _lib.check(rc, "haar_denoise_2d")
+    return out

@@ -417,8 +417,8 @@ int haar_dwt_1d(const haar_desc* x, const haar_desc* coef, int levels, void* wor
                      aligned(p.src, p.s_bs, p.s_rs, dt_size(tin), vec_align_img(tin)) &&
                      aligned(p.dst, p.d_bs, p.d_rs, dt_size(coef->dtype),
                              vec_align_coef(coef->dtype));
-    const cudaError_t e =
-        dispatch_dwt1d(tin, coef->dtype, p, chunk_for_levels(pl.lv[k]), vec, st);
+    const int cfg = (vec && wk % 256 == 0 && pl.lv[k] <= 8) ? kFast1 : chunk_for_levels(pl.lv[k]);
+    const cudaError_t e = dispatch_dwt1d(tin, coef->dtype, p, cfg, vec, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return HAAR_OK;
@@ -476,8 +476,8 @@ int haar_idwt_1d(const haar_desc* coef, const haar_desc* x, int levels, void* wo
                      aligned(p.src, p.s_bs, p.s_rs, dt_size(coef->dtype),
                              vec_align_coef(coef->dtype)) &&
                      aligned(p.dst, p.d_bs, p.d_rs, dt_size(tout), vec_align_img(tout));
-    const cudaError_t e =
-        dispatch_idwt1d(coef->dtype, tout, p, chunk_for_levels(pl.lv[k]), vec, st);
+    const int cfg = (vec && wk % 256 == 0 && pl.lv[k] <= 8) ? kFast1 : chunk_for_levels(pl.lv[k]);
+    const cudaError_t e = dispatch_idwt1d(coef->dtype, tout, p, cfg, vec, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return HAAR_OK;

@@ -54,8 +54,10 @@ inline int tile_w(int cfg) { return cfg == kT64x64 ? 64 : 128; }
 inline int tile_max_levels(int cfg) { return cfg == kT32x128 ? 5 : 6; }
 constexpr int kScalarTileLevels = 6;
 
-// 1D chunk shapes: 1024 samples (up to 10 fused levels) or 4096 (12).
-enum Chunk1Cfg { kC1024 = 0, kC4096 = 1 };
+// 1D chunk shapes: 1024 samples (up to 10 fused levels) or 4096 (12);
+// kFast1 selects the register/warp-shuffle kernels (haar_fast1d.cuh), valid
+// for lengths that are multiples of 256, aligned rows and at most 8 levels.
+enum Chunk1Cfg { kC1024 = 0, kC4096 = 1, kFast1 = 2 };
 inline int chunk_max_levels(int cfg) { return cfg == kC1024 ? 10 : 12; }
 
 // ---------------------------------------------------------------------------

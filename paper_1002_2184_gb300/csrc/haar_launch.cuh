@@ -3,6 +3,7 @@
 #pragma once
 
 #include "haar_internal.h"
+#include "haar_fast1d.cuh"
 #include "haar_fast2d.cuh"
 #include "haar_ragged.cuh"
 #include "haar_kernels.cuh"
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(NT) k_idwt1d(const Pass p) {
 
 template <typename Tin, typename Tout>
 cudaError_t dwt1d_t(Pass p, int cfg, bool vec, cudaStream_t s) {
+  if (cfg == kFast1) return dwt1d_fast_t<Tin, Tout>(p, true, s);
   const int CH = cfg == kC1024 ? 1024 : 4096;
   p.tiles_x = ceil_div(p.w, CH);
   p.tiles_y = 1;
@@ -210,6 +212,7 @@ cudaError_t dwt1d_t(Pass p, int cfg, bool vec, cudaStream_t s) {
 
 template <typename Tin, typename Tout>
 cudaError_t idwt1d_t(Pass p, int cfg, bool vec, cudaStream_t s) {
+  if (cfg == kFast1) return dwt1d_fast_t<Tin, Tout>(p, false, s);
   const int CH = cfg == kC1024 ? 1024 : 4096;
   p.tiles_x = ceil_div(p.w, CH);
   p.tiles_y = 1;

@@ -410,3 +410,42 @@ def test_planted_mistake_is_caught(name):
     impl = _mutants()[name]
     failed = [p.__name__ for p in PINS if not p(impl)]
     assert failed, f"mutant {name} passed every pin"
+
+
+# --------------------------------------------------------------------------
+# Wavelet shrinkage: closed-form limits.
+# --------------------------------------------------------------------------
+
+def test_shrink_limits_are_block_means_and_identity():
+    """With an infinite threshold every detail vanishes and the output is the
+    mean over each 2^L block (1D) or 2^L x 2^L block (2D) -- the Haar scaling
+    function; with threshold 0 the output is the input."""
+    rng = synth.rng(8, 0)
+    x = rng.standard_normal((3, 256))
+    for L in (1, 3, 8):
+        y = oracle.denoise1d(x, L, 1e30)
+        blocks = x.reshape(3, -1, 1 << L).mean(axis=-1)
+        assert np.allclose(y, np.repeat(blocks, 1 << L, axis=-1), atol=1e-13)
+        assert np.allclose(oracle.denoise1d(x, L, 0.0), x, atol=1e-13)
+    im = rng.standard_normal((2, 64, 96))
+    for L in (1, 2, 5):
+        y = oracle.denoise2d(im, L, 1e30)
+        b = 1 << L
+        means = im.reshape(2, 64 // b, b, 96 // b, b).mean(axis=(2, 4))
+        assert np.allclose(y, np.repeat(np.repeat(means, b, axis=1), b, axis=2), atol=1e-13)
+        assert np.allclose(oracle.denoise2d(im, L, 0.0, hard=True), im, atol=1e-13)
+
+
+def test_hard_shrink_keeps_large_details_exactly():
+    """A step edge has one large level-1 detail; with a threshold between
+    the noise-free details (0) and the edge detail, hard shrinkage returns
+    the signal unchanged and soft shrinkage moves it by exactly t/sqrt(2) at
+    the two samples of the edge pair."""
+    x = np.zeros(16)
+    x[5:] = 1.0  # edge inside the pair (4, 5)
+    y = oracle.denoise1d(x, 1, 0.1, hard=True)
+    assert np.allclose(y, x, atol=1e-15)
+    ys = oracle.denoise1d(x, 1, 0.1)
+    d = ys - x
+    assert np.allclose(d[[4, 5]], [0.1 / np.sqrt(2), -0.1 / np.sqrt(2)], atol=1e-15)
+    assert np.allclose(np.delete(d, [4, 5]), 0.0, atol=1e-15)
