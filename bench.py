@@ -442,6 +442,8 @@ def forms(api, synth, dev, world):
                         "gsamples_s": round(sc.n / (ms * 1e-3) / 1e9, 3),
                         "note": "launch-latency bound (two launches of 1 MiB traffic "
                                 "in total); graph replay; data resident in L2"}
+    res["signal_1d_batch"] = signal_batch_form(api, synth, dev)
+    res["denoise_2d"] = denoise2d_form(api, synth, dev)
 
     # precision form: 64 x 2048^2, 4 levels; bf16 / fp16 / u8-in vs fp32
     pc = synth.PrecisionBatch()
@@ -541,6 +543,71 @@ def grad_form(api, synth, dev):
             "unfused_autograd_ms": round(ms_unfused, 4),
             "plain_fp32_dwt_idwt_ms": round(ms_rt, 4),
             "fwd_bwd_over_plain_round_trip": round(ms_graph / ms_rt, 3)}
+
+
+def _hbm():
+    peaks = measured_peaks()
+    return (peaks or {}).get("hbm_gbs") or 6800.0
+
+
+def signal_batch_form(api, synth, dev):
+    """64 signals of 2^20 fp32 samples (the signal generator), 8 levels:
+    DWT + IDWT round trip and the one-pass shrinkage (soft threshold 1.0)."""
+    import torch
+    rows, n, L = 64, 1 << 20, 8
+    base = [torch.from_numpy(synth.signal_1d(n, synth.Signal1D.seed, i).astype(np.float32))
+            for i in range(4)]
+    x = torch.stack([base[i % 4] for i in range(rows)]).to(dev)
+    c = torch.empty_like(x)
+    y = torch.empty_like(x)
+    plan = api.Plan(x, c, L, y, one_d=True)
+    ms_rt = time_ms(lambda: (plan.dwt(), plan.idwt()), 20)
+    ms_dn = time_ms(lambda: api.denoise1d(x, L, 1.0, out=y), 20)
+    # the paper's comparison, existing vs fast, at scale: one level of the
+    # undecimated direct form (every convolution output computed, 12 B per
+    # sample) against the Fast Haar analysis (the decimated outputs only)
+    u = torch.empty((rows, 2, n), dtype=x.dtype, device=dev)
+    p1 = api.Plan(x, c, 1, y, one_d=True)
+    ms_direct = time_ms(lambda: api.swt1d(x, 1, out=u), 20)
+    ms_fast = time_ms(p1.dwt, 20)
+    same = bool(torch.equal(u[:, 1, ::2], c[:, n // 2:]))
+    px = rows * n
+    hbm = _hbm()
+    return {"workload": f"{rows} x 2^20 fp32 signals, {L} levels",
+            "existing_vs_fast_1_level": {"undecimated_ms": round(ms_direct, 4),
+                                         "fast_haar_ms": round(ms_fast, 4),
+                                         "ratio": round(ms_direct / ms_fast, 3),
+                                         "decimated_direct_equals_fast": same},
+            "round_trip_ms": round(ms_rt, 4),
+            "round_trip_gsamples_s": round(px / (ms_rt * 1e-3) / 1e9, 2),
+            "round_trip_frac_of_hbm": round(16.0 * px / (ms_rt * 1e-3) / 1e9 / hbm, 4),
+            "denoise_ms": round(ms_dn, 4),
+            "denoise_gsamples_s": round(px / (ms_dn * 1e-3) / 1e9, 2),
+            "denoise_frac_of_hbm": round(8.0 * px / (ms_dn * 1e-3) / 1e9 / hbm, 4),
+            "denoise_bytes_per_sample": 8}
+
+
+def denoise2d_form(api, synth, dev):
+    """One-pass soft shrinkage (t = 0.05, 5 levels) of 4 x 4096 x 4096 fp32
+    images next to the DWT + IDWT round trip of the same batch."""
+    import torch
+    cfg = synth.Image2D()
+    im = torch.from_numpy(synth.piecewise_smooth_image(cfg.h, cfg.w, cfg.seed, 0)
+                          .astype(np.float32)).to(dev)
+    x = im.expand(4, cfg.h, cfg.w).contiguous()
+    y = torch.empty_like(x)
+    c = torch.empty_like(x)
+    plan = api.Plan(x, c, cfg.levels, y)
+    ms_rt = time_ms(lambda: (plan.dwt(), plan.idwt()), 20)
+    ms_dn = time_ms(lambda: api.denoise2d(x, cfg.levels, 0.05, out=y), 20)
+    px = x.numel()
+    hbm = _hbm()
+    return {"workload": f"4 x {cfg.h}x{cfg.w} fp32 images, {cfg.levels} levels, soft t=0.05",
+            "denoise_ms": round(ms_dn, 4),
+            "denoise_gsamples_s": round(px / (ms_dn * 1e-3) / 1e9, 2),
+            "denoise_frac_of_hbm": round(8.0 * px / (ms_dn * 1e-3) / 1e9 / hbm, 4),
+            "round_trip_ms": round(ms_rt, 4),
+            "speedup_vs_round_trip": round(ms_rt / ms_dn, 3)}
 
 
 def ragged_form(api, synth, dev, dense_fp32_gsamples):

@@ -216,6 +216,23 @@ int haar_ragged_status(const haar_ragged_plan *plan, void *workspace, int *statu
 int haar_ragged_plan_destroy(haar_ragged_plan *plan);
 
 /* ------------------------------------------------------------------------
+ * The undecimated (stationary) Haar transform, 1D: the bank of Section II,
+ * Fig. 1 with the down-sampler removed -- every convolution output is kept,
+ * the filters dilated by 2^(l-1) at level l (a trous), boundaries periodic:
+ *   a_l[k] = (a_{l-1}[k] + a_{l-1}[k+s]) / sqrt(2),
+ *   d_l[k] = (a_{l-1}[k+s] - a_{l-1}[k]) / sqrt(2),   s = 2^(l-1)
+ * It is the direct form whose decimated outputs the Fast Haar bank never
+ * computes: d_l[2^l m] and a_L[2^L m] are the decimated transform's
+ * coefficients.  x: rows x n contiguous; coef: rows x (levels + 1) x n
+ * contiguous, row 0 = a_L, row l = d_l.  F32 or F64; 1 <= levels <= 10;
+ * n >= 2^levels.  The inverse averages the two reconstructions of each
+ * sample: a_{l-1}[k] = ((a_l[k] - d_l[k]) + (a_l[k-s] + d_l[k-s])) / (2 sqrt 2). */
+int haar_swt_1d(const void *x, void *coef, int dtype, int64_t rows, int64_t n, int levels,
+                void *cuda_stream);
+int haar_iswt_1d(const void *coef, void *x, int dtype, int64_t rows, int64_t n, int levels,
+                 void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Wavelet shrinkage in one pass (the paper's denoising use case for
  * biosignals and medical images, Section VI; the shrinkage rule is the
  * standard one, not the paper's): y = W^T shrink(W x), where every detail

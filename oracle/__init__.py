@@ -244,6 +244,40 @@ def denoise_loss_grad(x, levels: int, t: float, lam: float) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Undecimated (stationary) transform: the bank of Fig. 1 without the
+# down-sampler, filters dilated by 2^(l-1) at level l, periodic boundary.
+# Output (..., L + 1, n): row 0 = a_L, row l = d_l.
+# --------------------------------------------------------------------------
+
+def swt1d(x, levels: int) -> np.ndarray:
+    x = _f64(x)
+    s2 = 1.0 / np.sqrt(2.0)
+    a = x.copy()
+    out = np.empty(x.shape[:-1] + (levels + 1, x.shape[-1]))
+    for l in range(1, levels + 1):
+        s = 1 << (l - 1)
+        nxt = np.roll(a, -s, axis=-1)  # a[k + s], wrapping around
+        out[..., l, :] = (nxt - a) * s2
+        a = (a + nxt) * s2
+    out[..., 0, :] = a
+    return out
+
+
+def iswt1d(c, levels: int) -> np.ndarray:
+    c = _f64(c)
+    s2 = 1.0 / np.sqrt(2.0)
+    a = c[..., 0, :].copy()
+    for l in range(levels, 0, -1):
+        s = 1 << (l - 1)
+        d = c[..., l, :]
+        # two estimates of a_{l-1}[k]: from position k and from position k - s
+        e1 = (a - d) * s2
+        e2 = np.roll((a + d) * s2, s, axis=-1)
+        a = 0.5 * (e1 + e2)
+    return a
+
+
+# --------------------------------------------------------------------------
 # Wavelet shrinkage (denoising): threshold every detail coefficient, keep the
 # low band, transform back.
 # --------------------------------------------------------------------------
@@ -292,5 +326,5 @@ __all__ = [
     "lib", "analysis_1d", "synthesis_1d", "polyphase_analysis_1d",
     "polyphase_synthesis_1d", "dwt1d", "idwt1d", "dwt2d", "idwt2d",
     "detail_mask_1d", "detail_mask_2d", "soft_threshold", "denoise_loss",
-    "denoise_loss_grad", "shrink", "denoise1d", "denoise2d", "rel_l2", "max_abs",
+    "denoise_loss_grad", "swt1d", "iswt1d", "shrink", "denoise1d", "denoise2d", "rel_l2", "max_abs",
 ]

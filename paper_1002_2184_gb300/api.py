@@ -308,3 +308,36 @@ def denoise2d(x: torch.Tensor, levels: int, threshold: float, hard: bool = False
                                  _stream(x))
     _lib.check(rc, "haar_denoise_2d")
     return out
+
+
+def swt1d(x: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Undecimated Haar transform of every row of (..., n) (contiguous):
+    returns (..., levels + 1, n) with [a_L, d_1, ..., d_L]."""
+    if not x.is_contiguous():
+        raise ValueError("swt1d needs a contiguous input")
+    n = x.shape[-1]
+    rows = x.numel() // max(n, 1)
+    shape = tuple(x.shape[:-1]) + (levels + 1, n)
+    out = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else out
+    lib = _lib.load()
+    with torch.cuda.device(x.device):
+        rc = lib.haar_swt_1d(x.data_ptr(), out.data_ptr(), haar_dtype(x.dtype), rows, n, levels,
+                             _stream(x))
+    _lib.check(rc, "haar_swt_1d")
+    return out
+
+
+def iswt1d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Inverse of :func:`swt1d`."""
+    if not c.is_contiguous():
+        raise ValueError("iswt1d needs a contiguous input")
+    n = c.shape[-1]
+    shape = tuple(c.shape[:-2]) + (n,)
+    rows = c.numel() // max((levels + 1) * n, 1)
+    out = torch.empty(shape, dtype=c.dtype, device=c.device) if out is None else out
+    lib = _lib.load()
+    with torch.cuda.device(c.device):
+        rc = lib.haar_iswt_1d(c.data_ptr(), out.data_ptr(), haar_dtype(c.dtype), rows, n, levels,
+                              _stream(c))
+    _lib.check(rc, "haar_iswt_1d")
+    return out

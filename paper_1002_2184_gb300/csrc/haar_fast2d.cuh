@@ -260,7 +260,8 @@ __device__ __forceinline__ void dwt_level6(const Img2& im, A tl, A tr, A bl, A b
 
 // ---------------------------------------------------------------------------
 // Synthesis of one 32 x 32 block by one warp (any L <= 6): every load is
-// issued first; no communication between lanes.
+// issued first -- the coarse coefficients, needed first, then the level-2
+// and level-1 details -- and the lanes do not communicate.
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout, int L, typename Epi = EpiStore>
 __device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t x0, int lane,
@@ -272,13 +273,6 @@ __device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t
   const int64_t py = y0 + 4 * ty, px = x0 + 8 * tx;
 
   A d1x[2][4], d1y[2][4], d1z[2][4];
-#pragma unroll
-  for (int rp = 0; rp < 2; ++rp) {
-    const int64_t row = (py >> 1) + rp, col = px >> 1;
-    load4(in.hx(1, row, col), d1x[rp]);
-    load4(in.hy(1, row, col), d1y[rp]);
-    load4(in.hh(1, row, col), d1z[rp]);
-  }
   A ll1[2][4];
   A ll2[2];
   A d2x[2], d2y[2], d2z[2];
@@ -319,6 +313,13 @@ __device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t
     }
   }
 
+#pragma unroll
+  for (int rp = 0; rp < 2; ++rp) {
+    const int64_t row = (py >> 1) + rp, col = px >> 1;
+    load4(in.hx(1, row, col), d1x[rp]);
+    load4(in.hy(1, row, col), d1y[rp]);
+    load4(in.hh(1, row, col), d1z[rp]);
+  }
   // ---- coarse levels: walk down to this lane's LL2 pair ----
   if constexpr (L >= 3) {
     A v = llL;

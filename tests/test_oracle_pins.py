@@ -449,3 +449,33 @@ def test_hard_shrink_keeps_large_details_exactly():
     d = ys - x
     assert np.allclose(d[[4, 5]], [0.1 / np.sqrt(2), -0.1 / np.sqrt(2)], atol=1e-15)
     assert np.allclose(np.delete(d, [4, 5]), 0.0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Undecimated (stationary) transform.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,levels", [(16, 1), (64, 3), (256, 5), (1024, 10)])
+def test_swt_decimates_to_the_dwt(n, levels):
+    """Keeping every 2^l-th sample of level l of the undecimated transform
+    gives the decimated (Mallat) coefficients of the pinned DWT."""
+    x = synth.signal_1d(n, seed=9, index=n)
+    u = oracle.swt1d(x, levels)
+    c = oracle.dwt1d(x, levels)
+    for l in range(1, levels + 1):
+        assert np.allclose(u[l, :: 1 << l], c[n >> l: n >> (l - 1)], atol=1e-13)
+    assert np.allclose(u[0, :: 1 << levels], c[: n >> levels], atol=1e-13)
+
+
+def test_swt_is_shift_equivariant_energy_and_pr():
+    rng = synth.rng(10, 0)
+    x = rng.standard_normal((3, 128))
+    L = 5
+    u = oracle.swt1d(x, L)
+    assert np.allclose(oracle.swt1d(np.roll(x, 1, axis=-1), L), np.roll(u, 1, axis=-1),
+                       atol=1e-13)
+    # sum_l |d_l|^2 / 2^l + |a_L|^2 / 2^L = |x|^2 (each level doubles energy)
+    e = sum(np.sum(u[:, l] ** 2, axis=-1) / 2.0 ** l for l in range(1, L + 1))
+    e = e + np.sum(u[:, 0] ** 2, axis=-1) / 2.0 ** L
+    assert np.allclose(e, np.sum(x ** 2, axis=-1), rtol=1e-13)
+    assert np.allclose(oracle.iswt1d(u, L), x, atol=1e-13)
