@@ -443,6 +443,7 @@ def forms(api, synth, dev, world):
                         "note": "launch-latency bound (two launches of 1 MiB traffic "
                                 "in total); graph replay; data resident in L2"}
     res["signal_1d_batch"] = signal_batch_form(api, synth, dev)
+    res["volume_3d"] = volume_form(api, synth, dev)
     res["denoise_2d"] = denoise2d_form(api, synth, dev)
 
     # precision form: 64 x 2048^2, 4 levels; bf16 / fp16 / u8-in vs fp32
@@ -585,6 +586,24 @@ def signal_batch_form(api, synth, dev):
             "denoise_gsamples_s": round(px / (ms_dn * 1e-3) / 1e9, 2),
             "denoise_frac_of_hbm": round(8.0 * px / (ms_dn * 1e-3) / 1e9 / hbm, 4),
             "denoise_bytes_per_sample": 8}
+
+
+def volume_form(api, synth, dev):
+    """3D: a 256^3 fp32 volume (slices of the image generator), 3 levels,
+    DWT + IDWT round trip."""
+    import torch
+    side, L = 256, 3
+    sl = [torch.from_numpy(synth.piecewise_smooth_image(side, side, 77, i).astype(np.float32))
+          for i in range(8)]
+    x = torch.stack([sl[i % 8] for i in range(side)]).to(dev)
+    c = torch.empty_like(x)
+    y = torch.empty_like(x)
+    ms = time_ms(lambda: (api.dwt3d(x, L, out=c), api.idwt3d(c, L, out=y)), 20)
+    ok = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)) <= 1e-6
+    px = x.numel()
+    return {"workload": f"{side}^3 fp32 volume, {L} levels, DWT + IDWT",
+            "ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
+            "frac_of_hbm": round(16.0 * px / (ms * 1e-3) / 1e9 / _hbm(), 4), "round_trip_ok": ok}
 
 
 def denoise2d_form(api, synth, dev):

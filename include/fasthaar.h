@@ -150,6 +150,33 @@ int haar_dwt_2d_noalloc(const haar_desc *x, const haar_desc *coef, int levels,
                         void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * 3D (volumes, video): the bank along x, then y, then z at every level, on
+ * the current low-pass region (the 2D recursion with a third axis; not in
+ * the paper, which treats signals and images).  Octant (bz, by, bx) of level
+ * l -- b = 0 low, 1 high along that axis -- sits at (bz D_l/2, by H_l/2,
+ * bx W_l/2) inside the level's region (D_l, H_l, W_l) = (d, h, w) / 2^(l-1).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  void *ptr;
+  int32_t dtype;     /* haar_dtype: F32, BF16, F16 or F64 */
+  int32_t reserved;  /* must be 0 */
+  int64_t batch, d, h, w;
+  int64_t batch_stride, plane_stride, row_stride; /* elements */
+} haar_desc3;
+
+/* Workspace of a 3D transform deeper than 3 levels (3 fuse per launch). */
+int haar_workspace_size_3d(const haar_desc3 *x, int levels, size_t *bytes);
+
+/* 3D analysis / synthesis.  d, h, w divisible by 2^levels; w a multiple of 8
+ * (rows move 8 samples at a time), and every chained pass must keep w >> 3k
+ * a multiple of 8; rows 16-byte aligned.  dtypes: equal storage types, or
+ * F32 with BF16/F16 (either direction); F64 only with F64. */
+int haar_dwt_3d(const haar_desc3 *x, const haar_desc3 *coef, int levels, void *workspace,
+                size_t workspace_bytes, void *cuda_stream);
+int haar_idwt_3d(const haar_desc3 *coef, const haar_desc3 *x, int levels, void *workspace,
+                 size_t workspace_bytes, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Ragged batches: many 2D images of different sizes and level counts in one
  * persistent launch.  Images live anywhere inside one input buffer and one
  * output buffer (element offsets from the two base pointers); the output of

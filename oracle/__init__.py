@@ -48,6 +48,11 @@ def lib() -> ctypes.CDLL:
             f.argtypes = [_DP, ctypes.c_long, ctypes.c_long, ctypes.c_int, _DP,
                           ctypes.c_int]
             f.restype = ctypes.c_int
+        for name in ("oracle_dwt_3d", "oracle_idwt_3d"):
+            f = getattr(L, name)
+            f.argtypes = [_DP, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_int, _DP,
+                          ctypes.c_int]
+            f.restype = ctypes.c_int
         _LIB = L
     return _LIB
 
@@ -174,6 +179,35 @@ def idwt2d(c, levels: int, detail_sign: int = 1) -> np.ndarray:
         dst = np.empty((h, w))
         _check(lib().oracle_idwt_2d(_p(src), h, w, levels, _p(dst),
                                     detail_sign), "idwt_2d")
+        out[i] = dst
+    return out.reshape(c.shape)
+
+
+def dwt3d(x, levels: int, detail_sign: int = 1) -> np.ndarray:
+    """Multi-level separable 3D analysis over the last three axes (octant
+    Mallat layout; not in the paper)."""
+    x = _f64(x)
+    d, h, w = x.shape[-3:]
+    flat = x.reshape(-1, d, h, w)
+    out = np.empty_like(flat)
+    for i in range(flat.shape[0]):
+        src = np.ascontiguousarray(flat[i])
+        dst = np.empty((d, h, w))
+        _check(lib().oracle_dwt_3d(_p(src), d, h, w, levels, _p(dst), detail_sign), "dwt_3d")
+        out[i] = dst
+    return out.reshape(x.shape)
+
+
+def idwt3d(c, levels: int, detail_sign: int = 1) -> np.ndarray:
+    """Inverse of :func:`dwt3d`."""
+    c = _f64(c)
+    d, h, w = c.shape[-3:]
+    flat = c.reshape(-1, d, h, w)
+    out = np.empty_like(flat)
+    for i in range(flat.shape[0]):
+        src = np.ascontiguousarray(flat[i])
+        dst = np.empty((d, h, w))
+        _check(lib().oracle_idwt_3d(_p(src), d, h, w, levels, _p(dst), detail_sign), "idwt_3d")
         out[i] = dst
     return out.reshape(c.shape)
 
@@ -324,7 +358,7 @@ def max_abs(a, ref) -> float:
 
 __all__ = [
     "lib", "analysis_1d", "synthesis_1d", "polyphase_analysis_1d",
-    "polyphase_synthesis_1d", "dwt1d", "idwt1d", "dwt2d", "idwt2d",
+    "polyphase_synthesis_1d", "dwt1d", "idwt1d", "dwt2d", "idwt2d", "dwt3d", "idwt3d",
     "detail_mask_1d", "detail_mask_2d", "soft_threshold", "denoise_loss",
     "denoise_loss_grad", "swt1d", "iswt1d", "shrink", "denoise1d", "denoise2d", "rel_l2", "max_abs",
 ]

@@ -283,3 +283,95 @@ fail:
   free(line); free(lo); free(hi);
   return -1;
 }
+
+/* Multi-level separable 3D analysis of a d x h x w volume (index
+ * (z * h + y) * w + x): per level, on the current low-pass region, the
+ * analysis stage along x for every (z, y) line, then along y for every
+ * (z, x) line, then along z for every (y, x) line; each splits the region
+ * into low (first half) and high (second half).  The same recursion as the
+ * 2D transform, with a third axis; not in the paper. */
+int oracle_dwt_3d(const double *x, long d, long h, long w, int levels, double *out,
+                  int detail_sign) {
+  if (!is_pow2_divisible(d, levels) || !is_pow2_divisible(h, levels) ||
+      !is_pow2_divisible(w, levels))
+    return -1;
+  if (d == 0 || h == 0 || w == 0) return 0;
+  long big = d > h ? d : h;
+  big = big > w ? big : w;
+  double *line = malloc(sizeof(double) * (size_t)big);
+  double *lo = malloc(sizeof(double) * (size_t)big);
+  double *hi = malloc(sizeof(double) * (size_t)big);
+  if (!line || !lo || !hi) { free(line); free(lo); free(hi); return -1; }
+  memcpy(out, x, sizeof(double) * (size_t)(d * h * w));
+#define AT(z, y, xx) out[((z) * h + (y)) * w + (xx)]
+  for (int l = 1; l <= levels; ++l) {
+    long dl = d >> (l - 1), hl = h >> (l - 1), wl = w >> (l - 1);
+    for (long z = 0; z < dl; ++z)
+      for (long y = 0; y < hl; ++y) {
+        for (long i = 0; i < wl; ++i) line[i] = AT(z, y, i);
+        if (oracle_analysis_1d(line, wl, lo, hi, detail_sign) != 0) goto fail3;
+        for (long i = 0; i < wl / 2; ++i) { AT(z, y, i) = lo[i]; AT(z, y, i + wl / 2) = hi[i]; }
+      }
+    for (long z = 0; z < dl; ++z)
+      for (long xx = 0; xx < wl; ++xx) {
+        for (long i = 0; i < hl; ++i) line[i] = AT(z, i, xx);
+        if (oracle_analysis_1d(line, hl, lo, hi, detail_sign) != 0) goto fail3;
+        for (long i = 0; i < hl / 2; ++i) { AT(z, i, xx) = lo[i]; AT(z, i + hl / 2, xx) = hi[i]; }
+      }
+    for (long y = 0; y < hl; ++y)
+      for (long xx = 0; xx < wl; ++xx) {
+        for (long i = 0; i < dl; ++i) line[i] = AT(i, y, xx);
+        if (oracle_analysis_1d(line, dl, lo, hi, detail_sign) != 0) goto fail3;
+        for (long i = 0; i < dl / 2; ++i) { AT(i, y, xx) = lo[i]; AT(i + dl / 2, y, xx) = hi[i]; }
+      }
+  }
+  free(line); free(lo); free(hi);
+  return 0;
+fail3:
+  free(line); free(lo); free(hi);
+  return -1;
+}
+
+/* Multi-level 3D synthesis: coarsest level first; within a level the z, y
+ * and x stages are undone in that order. */
+int oracle_idwt_3d(const double *c, long d, long h, long w, int levels, double *out,
+                   int detail_sign) {
+  if (!is_pow2_divisible(d, levels) || !is_pow2_divisible(h, levels) ||
+      !is_pow2_divisible(w, levels))
+    return -1;
+  if (d == 0 || h == 0 || w == 0) return 0;
+  long big = d > h ? d : h;
+  big = big > w ? big : w;
+  double *line = malloc(sizeof(double) * (size_t)big);
+  double *lo = malloc(sizeof(double) * (size_t)big);
+  double *hi = malloc(sizeof(double) * (size_t)big);
+  if (!line || !lo || !hi) { free(line); free(lo); free(hi); return -1; }
+  memcpy(out, c, sizeof(double) * (size_t)(d * h * w));
+  for (int l = levels; l >= 1; --l) {
+    long dl = d >> (l - 1), hl = h >> (l - 1), wl = w >> (l - 1);
+    for (long y = 0; y < hl; ++y)
+      for (long xx = 0; xx < wl; ++xx) {
+        for (long i = 0; i < dl / 2; ++i) { lo[i] = AT(i, y, xx); hi[i] = AT(i + dl / 2, y, xx); }
+        if (oracle_synthesis_1d(lo, hi, dl / 2, line, detail_sign) != 0) goto fail4;
+        for (long i = 0; i < dl; ++i) AT(i, y, xx) = line[i];
+      }
+    for (long z = 0; z < dl; ++z)
+      for (long xx = 0; xx < wl; ++xx) {
+        for (long i = 0; i < hl / 2; ++i) { lo[i] = AT(z, i, xx); hi[i] = AT(z, i + hl / 2, xx); }
+        if (oracle_synthesis_1d(lo, hi, hl / 2, line, detail_sign) != 0) goto fail4;
+        for (long i = 0; i < hl; ++i) AT(z, i, xx) = line[i];
+      }
+    for (long z = 0; z < dl; ++z)
+      for (long y = 0; y < hl; ++y) {
+        for (long i = 0; i < wl / 2; ++i) { lo[i] = AT(z, y, i); hi[i] = AT(z, y, i + wl / 2); }
+        if (oracle_synthesis_1d(lo, hi, wl / 2, line, detail_sign) != 0) goto fail4;
+        for (long i = 0; i < wl; ++i) AT(z, y, i) = line[i];
+      }
+  }
+#undef AT
+  free(line); free(lo); free(hi);
+  return 0;
+fail4:
+  free(line); free(lo); free(hi);
+  return -1;
+}

@@ -49,6 +49,21 @@ class HaarDesc(ctypes.Structure):
     ]
 
 
+class HaarDesc3(ctypes.Structure):
+    _fields_ = [
+        ("ptr", ctypes.c_void_p),
+        ("dtype", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("batch", ctypes.c_int64),
+        ("d", ctypes.c_int64),
+        ("h", ctypes.c_int64),
+        ("w", ctypes.c_int64),
+        ("batch_stride", ctypes.c_int64),
+        ("plane_stride", ctypes.c_int64),
+        ("row_stride", ctypes.c_int64),
+    ]
+
+
 class HaarRaggedItem(ctypes.Structure):
     _fields_ = [
         ("in_offset", ctypes.c_int64),
@@ -78,6 +93,7 @@ _LIB = None
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _DP = ctypes.POINTER(HaarDesc)
+_D3 = ctypes.POINTER(HaarDesc3)
 SIGNATURES = {
     "haar_version": (ctypes.c_int, []),
     "haar_last_cuda_error": (ctypes.c_int, []),
@@ -88,6 +104,9 @@ SIGNATURES = {
     "haar_idwt_1d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_dwt_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_idwt_2d": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "haar_workspace_size_3d": (ctypes.c_int, [_D3, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "haar_dwt_3d": (ctypes.c_int, [_D3, _D3, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "haar_idwt_3d": (ctypes.c_int, [_D3, _D3, ctypes.c_int, _P, ctypes.c_size_t, _P]),
     "haar_dwt_2d_noalloc": (ctypes.c_int, [_DP, _DP, ctypes.c_int, _P]),
     "haar_ragged_plan_create": (ctypes.c_int, [ctypes.POINTER(HaarRaggedItem), ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_int,

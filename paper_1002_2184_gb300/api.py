@@ -341,3 +341,47 @@ def iswt1d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None) -> 
                               _stream(c))
     _lib.check(rc, "haar_iswt_1d")
     return out
+
+
+def describe3(t: torch.Tensor) -> _lib.HaarDesc3:
+    """The haar_desc3 of a (..., d, h, w) CUDA tensor with contiguous rows."""
+    if not t.is_cuda:
+        raise ValueError("libfasthaar works on CUDA tensors only")
+    if t.dim() < 3:
+        raise ValueError("a volume needs three dimensions")
+    if t.numel() and t.shape[-1] > 1 and t.stride(-1) != 1:
+        raise ValueError("rows must be contiguous (last stride 1)")
+    d, h, w = t.shape[-3:]
+    rs = t.stride(-2) if h > 1 else w
+    zs = t.stride(-3) if d > 1 else h * rs
+    batch, bs = _lead_stride(t, t.dim() - 3, d * zs)
+    return _lib.HaarDesc3(t.data_ptr(), haar_dtype(t.dtype), 0, batch, d, h, w, bs, zs, rs)
+
+
+def _run3(fn_name: str, src: torch.Tensor, dst: torch.Tensor, levels: int) -> torch.Tensor:
+    lib = _lib.load()
+    ds, dd = describe3(src), describe3(dst)
+    n = ctypes.c_size_t(0)
+    _lib.check(lib.haar_workspace_size_3d(ctypes.byref(ds), levels, ctypes.byref(n)),
+               "haar_workspace_size_3d")
+    ws = torch.empty(n.value, dtype=torch.uint8, device=src.device) if n.value else None
+    with torch.cuda.device(src.device):
+        rc = getattr(lib, fn_name)(ctypes.byref(ds), ctypes.byref(dd), levels,
+                                   ws.data_ptr() if ws is not None else None, n.value,
+                                   _stream(src))
+    _lib.check(rc, fn_name)
+    return dst
+
+
+def dwt3d(x: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
+          dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """Multi-level separable 3D analysis of (..., d, h, w) (octant layout)."""
+    out = _out_like(x, (dtype or x.dtype) if out is None else out.dtype, out)
+    return _run3("haar_dwt_3d", x, out, levels)
+
+
+def idwt3d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
+           dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """Inverse of :func:`dwt3d`."""
+    out = _out_like(c, (dtype or c.dtype) if out is None else out.dtype, out)
+    return _run3("haar_idwt_3d", c, out, levels)

@@ -1,0 +1,77 @@
+"""3D separable Haar transform on the GPU against the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1002_2184_gb300 import _lib, api, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+def volume(shape, seed, dtype=torch.float32):
+    b = int(np.prod(shape[:-3]))
+    d, h, w = shape[-3:]
+    arr = np.stack([np.stack([synth.piecewise_smooth_image(h, w, seed=seed, index=i * d + z)
+                              for z in range(d)]) for i in range(b)])
+    return torch.from_numpy(arr.reshape(shape)).to(DEV).to(dtype)
+
+
+CASES = [((1, 8, 8, 64), 1), ((1, 8, 8, 64), 2), ((2, 16, 32, 64), 3), ((1, 24, 40, 72), 3),
+         ((1, 32, 32, 128), 5), ((3, 8, 16, 128), 3), ((1, 64, 64, 64), 6)]
+
+
+@pytest.mark.parametrize("shape,levels", CASES)
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+def test_3d_matches_oracle(shape, levels, dt):
+    x = volume(shape, seed=levels, dtype=dt)
+    c = api.dwt3d(x, levels)
+    ref = oracle.dwt3d(x.double().cpu().numpy(), levels)
+    tol = 1e-6 if dt == torch.float32 else 1e-2
+    assert oracle.rel_l2(c.double().cpu().numpy(), ref) <= tol
+    y = api.idwt3d(c, levels)
+    yref = oracle.idwt3d(c.double().cpu().numpy(), levels)
+    assert oracle.rel_l2(y.double().cpu().numpy(), yref) <= tol
+    if dt == torch.float32:
+        assert oracle.rel_l2(y.double().cpu().numpy(), x.double().cpu().numpy()) <= 1e-6
+
+
+def test_3d_fp64_and_strided():
+    x = volume((2, 8, 16, 64), seed=3, dtype=torch.float64)
+    c = api.dwt3d(x, 3)
+    assert oracle.rel_l2(c.cpu().numpy(), oracle.dwt3d(x.cpu().numpy(), 3)) <= 1e-13
+    big = volume((1, 12, 20, 160), seed=4)
+    v = big[:, 2:10, 2:18, 32:96]   # plane stride 20*160, row stride 160
+    cv = api.dwt3d(v, 3)
+    assert oracle.rel_l2(cv.double().cpu().numpy(), oracle.dwt3d(v.double().cpu().numpy(), 3)) \
+        <= 1e-6
+
+
+def test_3d_constant_exact_zero_detail():
+    x = torch.full((1, 16, 16, 64), 0.25, device=DEV)
+    c = api.dwt3d(x, 3).cpu().numpy()[0]
+    low = c[:2, :2, :8]
+    assert np.count_nonzero(c) == low.size
+
+
+def test_3d_rejections():
+    lib = _lib.load()
+    st = torch.cuda.current_stream().cuda_stream
+    x = torch.zeros(1, 8, 8, 12, device=DEV)
+    assert lib.haar_dwt_3d(ctypes.byref(api.describe3(x)),
+                           ctypes.byref(api.describe3(torch.zeros_like(x))), 1, None, 0, st) \
+        == _lib.HAAR_ESHAPE
+    y = torch.zeros(1, 8, 8, 64, device=DEV)
+    assert lib.haar_dwt_3d(ctypes.byref(api.describe3(y)), ctypes.byref(api.describe3(y)), 1,
+                           None, 0, st) == _lib.HAAR_EALIAS
+    z = torch.zeros(1, 32, 32, 64, device=DEV)
+    assert lib.haar_dwt_3d(ctypes.byref(api.describe3(z)),
+                           ctypes.byref(api.describe3(torch.zeros_like(z))), 5, None, 0, st) \
+        == _lib.HAAR_EWORKSPACE
+    u = torch.zeros(1, 8, 8, 64, device=DEV, dtype=torch.uint8)
+    assert lib.haar_dwt_3d(ctypes.byref(api.describe3(u)),
+                           ctypes.byref(api.describe3(torch.zeros_like(y))), 1, None, 0, st) \
+        == _lib.HAAR_EDTYPE

@@ -479,3 +479,58 @@ def test_swt_is_shift_equivariant_energy_and_pr():
     e = e + np.sum(u[:, 0] ** 2, axis=-1) / 2.0 ** L
     assert np.allclose(e, np.sum(x ** 2, axis=-1), rtol=1e-13)
     assert np.allclose(oracle.iswt1d(u, L), x, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# 3D (volumes): textbook separable basis, constant input, Parseval, PR.
+# --------------------------------------------------------------------------
+
+def textbook_3d(d, h, w, levels):
+    n = d * h * w
+    B = np.zeros((n, n))
+
+    def put(z, y, x, vz, vy, vx):
+        B[(z * h + y) * w + x] = np.einsum("i,j,k->ijk", vz, vy, vx).ravel()
+
+    for l in range(1, levels + 1):
+        dl, hl, wl = d >> l, h >> l, w >> l
+        for z in range(dl):
+            for y in range(hl):
+                for x in range(wl):
+                    for bz in (0, 1):
+                        for by in (0, 1):
+                            for bx in (0, 1):
+                                if bz == by == bx == 0:
+                                    continue
+                                vz = _psi(d, l, z) if bz else _phi(d, l, z)
+                                vy = _psi(h, l, y) if by else _phi(h, l, y)
+                                vx = _psi(w, l, x) if bx else _phi(w, l, x)
+                                put(bz * dl + z, by * hl + y, bx * wl + x, vz, vy, vx)
+    dL, hL, wL = d >> levels, h >> levels, w >> levels
+    for z in range(dL):
+        for y in range(hL):
+            for x in range(wL):
+                put(z, y, x, _phi(d, levels, z), _phi(h, levels, y), _phi(w, levels, x))
+    return B
+
+
+@pytest.mark.parametrize("d,h,w,levels", [(2, 2, 2, 1), (4, 4, 4, 2), (2, 4, 8, 1),
+                                          (8, 4, 4, 2), (4, 8, 8, 2)])
+def test_3d_matches_textbook_basis(d, h, w, levels):
+    n = d * h * w
+    M = _matrix(lambda e: oracle.dwt3d(e.reshape(d, h, w), levels).ravel(), n)
+    assert np.allclose(M, textbook_3d(d, h, w, levels), rtol=0, atol=1e-14)
+
+
+def test_3d_constant_parseval_pr():
+    c = 0.5
+    for L in (1, 2, 3):
+        z = oracle.dwt3d(np.full((8, 16, 8), c), L)
+        low = z[: 8 >> L, : 16 >> L, : 8 >> L]
+        assert np.allclose(low, c * (2.0 ** 1.5) ** L, rtol=1e-14, atol=0)
+        assert np.count_nonzero(z) == low.size
+    rng = synth.rng(12, 0)
+    x = rng.standard_normal((2, 16, 8, 32))
+    y = oracle.dwt3d(x, 3)
+    assert abs(np.sum(y ** 2) / np.sum(x ** 2) - 1) < 1e-13
+    assert np.max(np.abs(oracle.idwt3d(y, 3) - x)) < 1e-13
