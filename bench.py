@@ -444,6 +444,7 @@ def forms(api, synth, dev, world):
                                 "in total); graph replay; data resident in L2"}
     res["signal_1d_batch"] = signal_batch_form(api, synth, dev)
     res["volume_3d"] = volume_form(api, synth, dev)
+    res["filter_bank_1d"] = filter_form(api, synth, dev)
     res["denoise_2d"] = denoise2d_form(api, synth, dev)
 
     # precision form: 64 x 2048^2, 4 levels; bf16 / fp16 / u8-in vs fp32
@@ -586,6 +587,29 @@ def signal_batch_form(api, synth, dev):
             "denoise_gsamples_s": round(px / (ms_dn * 1e-3) / 1e9, 2),
             "denoise_frac_of_hbm": round(8.0 * px / (ms_dn * 1e-3) / 1e9 / hbm, 4),
             "denoise_bytes_per_sample": 8}
+
+
+def filter_form(api, synth, dev):
+    """The same polyphase bank with longer orthonormal low-pass filters:
+    64 x 2^20 fp32 signals, 8 levels, DWT + IDWT, K = 2 (Haar) and 4
+    (Daubechies-4) through the general K-tap kernels."""
+    import torch
+    rows, n, L = 64, 1 << 20, 8
+    base = [torch.from_numpy(synth.signal_1d(n, synth.Signal1D.seed, i).astype(np.float32))
+            for i in range(4)]
+    x = torch.stack([base[i % 4] for i in range(rows)]).to(dev)
+    c = torch.empty_like(x)
+    y = torch.empty_like(x)
+    px = rows * n
+    out = {"workload": f"{rows} x 2^20 fp32 signals, {L} levels, DWT + IDWT, periodic"}
+    for name, taps in (("haar_k2", api.HAAR2), ("daubechies4_k4", api.DAUBECHIES4)):
+        ms = time_ms(lambda: (api.filter_dwt1d(x, L, taps, out=c),
+                              api.filter_idwt1d(c, L, taps, out=y)), 20)
+        ok = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)) <= 1e-6
+        out[name] = {"ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
+                     "frac_of_hbm": round(16.0 * px / (ms * 1e-3) / 1e9 / _hbm(), 4),
+                     "round_trip_ok": ok}
+    return out
 
 
 def volume_form(api, synth, dev):

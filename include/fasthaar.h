@@ -243,6 +243,22 @@ int haar_ragged_status(const haar_ragged_plan *plan, void *workspace, int *statu
 int haar_ragged_plan_destroy(haar_ragged_plan *plan);
 
 /* ------------------------------------------------------------------------
+ * Longer orthogonal filters through the same down-sample-first polyphase
+ * identity (Section III, Eq. 7 states the split for a general filter): the
+ * two-channel bank for an even-length orthonormal low-pass h[0..K-1],
+ * K in {2, 4, 6, 8} (e.g. Daubechies-4), 1D, periodic boundary, multi-level
+ * Mallat layout [a_L | d_L | ... | d_1]:
+ *   a[n] = sum_k h[k] x[(2n+k) mod N],   d[n] = sum_k g[k] x[(2n+k) mod N],
+ *   g[k] = (-1)^(k+1) h[K-1-k]   (K = 2 gives the Haar detail sign of Eq. 9).
+ * Only the decimated outputs are computed.  x, coef: rows x n contiguous,
+ * F32 or F64; n divisible by 2^levels; 1 <= levels <= 10; `lowpass` is a
+ * host array of ntaps doubles (orthonormality is the caller's to ensure). */
+int haar_filter_dwt_1d(const void *x, void *coef, int dtype, int64_t rows, int64_t n, int levels,
+                       const double *lowpass, int ntaps, void *cuda_stream);
+int haar_filter_idwt_1d(const void *coef, void *x, int dtype, int64_t rows, int64_t n,
+                        int levels, const double *lowpass, int ntaps, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * The undecimated (stationary) Haar transform, 1D: the bank of Section II,
  * Fig. 1 with the down-sampler removed -- every convolution output is kept,
  * the filters dilated by 2^(l-1) at level l (a trous), boundaries periodic:

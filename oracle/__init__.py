@@ -278,6 +278,73 @@ def denoise_loss_grad(x, levels: int, t: float, lam: float) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# General orthonormal two-channel bank (K taps), periodic boundary: the
+# definition -- circular correlation with h and g, keep every other output
+# -- and its adjoint.  g[k] = (-1)^(k+1) h[K-1-k].
+# --------------------------------------------------------------------------
+
+def qmf_highpass(h) -> np.ndarray:
+    h = np.asarray(h, dtype=np.float64)
+    K = h.size
+    return np.array([(-1.0) ** (k + 1) * h[K - 1 - k] for k in range(K)])
+
+
+def filter_analysis_1d(x, h):
+    x = _f64(x)
+    h = np.asarray(h, dtype=np.float64)
+    g = qmf_highpass(h)
+    n = x.shape[-1]
+    lo = np.zeros(x.shape[:-1] + (n // 2,))
+    hi = np.zeros_like(lo)
+    for k in range(h.size):
+        idx = (2 * np.arange(n // 2) + k) % n
+        lo += h[k] * x[..., idx]
+        hi += g[k] * x[..., idx]
+    return lo, hi
+
+
+def filter_synthesis_1d(lo, hi, h):
+    lo, hi = _f64(lo), _f64(hi)
+    h = np.asarray(h, dtype=np.float64)
+    g = qmf_highpass(h)
+    m = lo.shape[-1]
+    n = 2 * m
+    x = np.zeros(lo.shape[:-1] + (n,))
+    for k in range(h.size):
+        idx = (2 * np.arange(m) + k) % n
+        # adjoint of the analysis: scatter-add each coefficient to the
+        # samples it was formed from
+        np.add.at(x, (..., idx), h[k] * lo + g[k] * hi)
+    return x
+
+
+def filter_dwt1d(x, levels: int, h) -> np.ndarray:
+    x = _f64(x)
+    n = x.shape[-1]
+    out = np.empty_like(x)
+    a = x.copy()
+    length = n
+    for _ in range(levels):
+        lo, hi = filter_analysis_1d(a, h)
+        out[..., length // 2: length] = hi
+        length //= 2
+        a = lo
+    out[..., :length] = a
+    return out
+
+
+def filter_idwt1d(c, levels: int, h) -> np.ndarray:
+    c = _f64(c)
+    n = c.shape[-1]
+    length = n >> levels
+    a = c[..., :length].copy()
+    for _ in range(levels):
+        a = filter_synthesis_1d(a, c[..., length: 2 * length], h)
+        length *= 2
+    return a
+
+
+# --------------------------------------------------------------------------
 # Undecimated (stationary) transform: the bank of Fig. 1 without the
 # down-sampler, filters dilated by 2^(l-1) at level l, periodic boundary.
 # Output (..., L + 1, n): row 0 = a_L, row l = d_l.
@@ -360,5 +427,6 @@ __all__ = [
     "lib", "analysis_1d", "synthesis_1d", "polyphase_analysis_1d",
     "polyphase_synthesis_1d", "dwt1d", "idwt1d", "dwt2d", "idwt2d", "dwt3d", "idwt3d",
     "detail_mask_1d", "detail_mask_2d", "soft_threshold", "denoise_loss",
-    "denoise_loss_grad", "swt1d", "iswt1d", "shrink", "denoise1d", "denoise2d", "rel_l2", "max_abs",
+    "denoise_loss_grad", "qmf_highpass", "filter_analysis_1d", "filter_synthesis_1d",
+    "filter_dwt1d", "filter_idwt1d", "swt1d", "iswt1d", "shrink", "denoise1d", "denoise2d", "rel_l2", "max_abs",
 ]

@@ -127,6 +127,12 @@ SIGNATURES = {
     "haar_soft_threshold_backward": (ctypes.c_int, [_DP, _DP, _DP, ctypes.c_int,
                                                     ctypes.c_double, _P, _P]),
     "haar_sq_diff_backward": (ctypes.c_int, [_DP, _DP, _DP, _DP, ctypes.c_double, _P, _P]),
+    "haar_filter_dwt_1d": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int, _P]),
+    "haar_filter_idwt_1d": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]),
     "haar_swt_1d": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.c_int, _P]),
     "haar_iswt_1d": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,

@@ -385,3 +385,35 @@ def idwt3d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None,
     """Inverse of :func:`dwt3d`."""
     out = _out_like(c, (dtype or c.dtype) if out is None else out.dtype, out)
     return _run3("haar_idwt_3d", c, out, levels)
+
+
+# Orthonormal Daubechies low-pass filters (closed forms).
+_R3 = 3.0 ** 0.5
+DAUBECHIES4 = tuple(v / (4.0 * 2.0 ** 0.5) for v in (1 + _R3, 3 + _R3, 3 - _R3, 1 - _R3))
+HAAR2 = (2.0 ** -0.5, 2.0 ** -0.5)
+
+
+def _filter_call(fn_name, src, dst, levels, taps):
+    if not (src.is_contiguous() and dst.is_contiguous()):
+        raise ValueError("filter transforms need contiguous tensors")
+    n = src.shape[-1]
+    rows = src.numel() // max(n, 1)
+    arr = (ctypes.c_double * len(taps))(*taps)
+    lib = _lib.load()
+    with torch.cuda.device(src.device):
+        rc = getattr(lib, fn_name)(src.data_ptr(), dst.data_ptr(), haar_dtype(src.dtype), rows, n,
+                                   levels, arr, len(taps), _stream(src))
+    _lib.check(rc, fn_name)
+    return dst
+
+
+def filter_dwt1d(x: torch.Tensor, levels: int, taps=DAUBECHIES4,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Multi-level 1D analysis with an orthonormal K-tap low-pass (periodic)."""
+    return _filter_call("haar_filter_dwt_1d", x, _out_like(x, x.dtype, out), levels, taps)
+
+
+def filter_idwt1d(c: torch.Tensor, levels: int, taps=DAUBECHIES4,
+                  out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Inverse of :func:`filter_dwt1d`."""
+    return _filter_call("haar_filter_idwt_1d", c, _out_like(c, c.dtype, out), levels, taps)

@@ -1,0 +1,52 @@
+"""The polyphase bank with longer orthonormal filters on the GPU against the
+FP64 oracle (K = 2, 4, 6, 8 taps, several level counts, chunk seams)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1002_2184_gb300 import _lib, api, synth
+from test_oracle_pins import _d4, lattice_lowpass
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+TAPS = {"haar": tuple(np.full(2, 1 / np.sqrt(2.0))), "d4": tuple(_d4()),
+        "lattice6": tuple(lattice_lowpass([0.3, -0.7, 1.1])),
+        "lattice8": tuple(lattice_lowpass([0.2, 0.5, -0.4, 0.9]))}
+
+
+@pytest.mark.parametrize("name", list(TAPS))
+@pytest.mark.parametrize("rows,n,levels", [(1, 64, 3), (3, 4096, 6), (2, 6144, 10),
+                                           (1, 1 << 16, 4), (2, 1024, 10), (1, 16, 4)])
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_filter_bank_matches_oracle(name, rows, n, levels, dt):
+    h = TAPS[name]
+    x = torch.from_numpy(np.stack([synth.signal_1d(n, seed=n, index=i) for i in range(rows)]))
+    x = x.to(DEV).to(dt)
+    c = api.filter_dwt1d(x, levels, h)
+    ref = oracle.filter_dwt1d(x.double().cpu().numpy(), levels, np.array(h))
+    tol = 1e-6 if dt == torch.float32 else 1e-13
+    assert oracle.rel_l2(c.double().cpu().numpy(), ref) <= tol
+    y = api.filter_idwt1d(c, levels, h)
+    yref = oracle.filter_idwt1d(c.double().cpu().numpy(), levels, np.array(h))
+    assert oracle.rel_l2(y.double().cpu().numpy(), yref) <= tol
+    assert oracle.rel_l2(y.double().cpu().numpy(), x.double().cpu().numpy()) <= tol
+
+
+def test_filter_rejections():
+    lib = _lib.load()
+    x = torch.zeros(2, 96, device=DEV)
+    y = torch.zeros_like(x)
+    st = torch.cuda.current_stream().cuda_stream
+    h4 = (ctypes.c_double * 4)(*TAPS["d4"])
+    assert lib.haar_filter_dwt_1d(x.data_ptr(), y.data_ptr(), 0, 2, 96, 6, h4, 4, st) \
+        == _lib.HAAR_ESHAPE
+    assert lib.haar_filter_dwt_1d(x.data_ptr(), y.data_ptr(), 0, 2, 96, 1, h4, 3, st) \
+        == _lib.HAAR_EINVAL
+    assert lib.haar_filter_dwt_1d(x.data_ptr(), x.data_ptr(), 0, 2, 96, 1, h4, 4, st) \
+        == _lib.HAAR_EALIAS
+    assert lib.haar_filter_dwt_1d(x.data_ptr(), y.data_ptr(), 0, 2, 96, 11, h4, 4, st) \
+        == _lib.HAAR_EINVAL

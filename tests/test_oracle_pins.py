@@ -534,3 +534,62 @@ def test_3d_constant_parseval_pr():
     y = oracle.dwt3d(x, 3)
     assert abs(np.sum(y ** 2) / np.sum(x ** 2) - 1) < 1e-13
     assert np.max(np.abs(oracle.idwt3d(y, 3) - x)) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# General orthonormal two-channel bank (longer filters, periodic boundary).
+# --------------------------------------------------------------------------
+
+def lattice_lowpass(angles):
+    """An orthonormal low-pass of length 2 * len(angles) built from a
+    paraunitary lattice of plane rotations and delays (an independent
+    construction: each stage preserves the double-shift orthogonality)."""
+    c, s = np.cos(angles[0]), np.sin(angles[0])
+    h0, h1 = np.array([c, s]), np.array([-s, c])
+    for th in angles[1:]:
+        c, s = np.cos(th), np.sin(th)
+        z2h1 = np.concatenate([[0.0, 0.0], h1])
+        h0p = np.concatenate([h0, [0.0, 0.0]])
+        h0, h1 = c * h0p + s * z2h1, -s * h0p + c * z2h1
+    return h0
+
+
+def _d4():
+    r3 = np.sqrt(3.0)
+    return np.array([1 + r3, 3 + r3, 3 - r3, 1 - r3]) / (4 * np.sqrt(2.0))
+
+
+def test_d4_closed_form_identities():
+    h = _d4()
+    assert abs(h.sum() - np.sqrt(2.0)) < 1e-15          # low pass, DC gain sqrt 2
+    assert abs(np.dot(h, h) - 1.0) < 1e-15              # unit norm
+    assert abs(h[0] * h[2] + h[1] * h[3]) < 1e-16       # orthogonal to its 2-shift
+    k = np.arange(4)
+    assert abs(np.dot(oracle.qmf_highpass(h), k)) < 1e-14  # two vanishing moments
+
+
+@pytest.mark.parametrize("taps", ["haar", "d4", "lattice6", "lattice8"])
+def test_filter_bank_is_orthonormal(taps):
+    h = {"haar": np.full(2, 1 / np.sqrt(2.0)), "d4": _d4(),
+         "lattice6": lattice_lowpass([0.3, -0.7, 1.1]),
+         "lattice8": lattice_lowpass([0.2, 0.5, -0.4, 0.9])}[taps]
+    n, L = 32, 3
+    W = _matrix(lambda e: oracle.filter_dwt1d(e, L, h), n)
+    assert np.allclose(W @ W.T, np.eye(n), atol=1e-13)
+    x = synth.rng(20, 0).standard_normal((2, n))
+    assert np.allclose(oracle.filter_idwt1d(oracle.filter_dwt1d(x, L, h), L, h), x, atol=1e-13)
+
+
+def test_filter_bank_with_haar_taps_is_the_haar_bank():
+    x = synth.signal_1d(256, seed=21)
+    h = np.full(2, 1 / np.sqrt(2.0))
+    assert np.allclose(oracle.filter_dwt1d(x, 5, h), oracle.dwt1d(x, 5), atol=1e-13)
+
+
+def test_d4_annihilates_linear_ramps():
+    """Daubechies-4 has two vanishing moments: every level-1 detail whose
+    four taps do not wrap around is exactly zero on a linear ramp."""
+    x = 3.0 + 0.25 * np.arange(64)
+    lo, hi = oracle.filter_analysis_1d(x, _d4())
+    assert np.allclose(hi[:-1], 0.0, atol=1e-13)
+    assert abs(hi[-1]) > 1.0  # the wrapped one sees the jump
