@@ -12,11 +12,13 @@
 //   g[k] = (-1)^(k+1) h[K-1-k]   (for K = 2 the detail sign of Eq. 9),
 //   x[2n + p] = sum_i h[p + 2i] a[n - i] + g[p + 2i] d[n - i],  i < K/2.
 //
-// Analysis: a block produces 2048 level-0 positions' worth of coefficients
-// (2048 / 2^l at level l); it stages the input samples it needs -- the chunk
-// plus a right halo of (K - 2)(2^L - 1) samples, wrapped -- in shared memory
-// and fuses every level there.  Synthesis: coarsest level first, each level
-// needing K/2 - 1 extra coefficients on the left.
+// Work is cut into chunks of 4096 level-0 positions (4096 / 2^l coefficients
+// at level l).  Analysis: the chunk plus a right halo of (K - 2)(2^L - 1)
+// samples (wrapped) is staged in shared memory with asynchronous 16-byte
+// copies and every level is fused there.  Synthesis: a_L and the window of
+// every d_l the chunk needs (K/2 - 1 extra coefficients per level on the
+// left) are staged in one go, the levels run coarsest first and level 1 is
+// written straight to the output.
 #include <cuda_runtime.h>
 
 #include "fasthaar.h"
@@ -25,11 +27,10 @@
 
 namespace fh {
 
-constexpr int kFChunk = 2048;
+constexpr int kFChunk = 4096;  // level-0 positions per block
 constexpr int kFMaxLevels = 10;
 constexpr int kFMaxTaps = 8;
-constexpr int kFHalo = (kFMaxTaps - 2) * ((1 << kFMaxLevels) - 1);  // analysis right halo
-constexpr int kFBuf = kFChunk + kFHalo;
+constexpr int kFThreads = 256;
 
 struct FilterArgs {
   const void* in;
@@ -40,124 +41,396 @@ struct FilterArgs {
   double h[kFMaxTaps], g[kFMaxTaps];
 };
 
-__device__ __forceinline__ int64_t fwrap(int64_t k, int64_t n) {
-  k %= n;
-  return k < 0 ? k + n : k;
+template <typename T> struct FVec2;
+template <> struct FVec2<float> { using type = float2; };
+template <> struct FVec2<double> { using type = double2; };
+
+// elements per 16-byte copy
+template <typename T>
+__host__ __device__ constexpr int fvec() { return 16 / (int)sizeof(T); }
+
+__host__ __device__ constexpr int fround(int v, int m) { return (v + m - 1) / m * m; }
+
+
+// ---- shared-memory footprints (host and device agree on these) ----
+// analysis: staged window (chunk + right halo) and one half-size buffer
+template <typename T, int K>
+__host__ __device__ constexpr int fdwt_cap_a(int L) {
+  return fround(kFChunk + (K - 2) * ((1 << L) - 1) + 2 * fvec<T>(), fvec<T>());
+}
+template <typename T, int K>
+__host__ __device__ constexpr int fdwt_cap_b(int L) {
+  return fround(kFChunk / 2 + (K - 2) * ((1 << L) - 1) / 2 + fvec<T>(), fvec<T>());
+}
+// synthesis: the window of level l (a_l or d_l) spans (chunk >> l) + at most
+// 2 (K/2 - 1) + 1 positions; every window is staged with a 16-byte slack and
+// room for the 8-wide reads of level 1 past its end
+template <typename T, int K>
+__host__ __device__ constexpr int fidwt_seg_cap(int l) {
+  return fround((kFChunk >> l) + 2 * (K / 2 - 1) + 2 + 2 * fvec<T>() + 8, fvec<T>());
+}
+template <typename T, int K>
+__host__ __device__ constexpr int fidwt_stage_cap(int L) {
+  int t = fidwt_seg_cap<T, K>(L);  // a_L
+  for (int l = 1; l <= L; ++l) t += fidwt_seg_cap<T, K>(l);
+  return t;
+}
+
+// ---- asynchronous global -> shared staging (cp.async, one wait at the end) ----
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Stage positions [s, s + cnt) of a sequence of period P stored at `row`
+// into dst[sh + i], sh = s mod (16 / sizeof(T)).  Inside the sequence and
+// with a 16-byte aligned row the copy is made of aligned 16-byte pieces
+// (which may also bring a few neighbours, inside [0, P)); otherwise, e.g. for
+// windows that wrap around, each element is copied on its own.  Returns sh.
+template <typename T>
+__device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s, int cnt, int tid,
+                                     int nt) {
+  constexpr int V = fvec<T>();
+  const int sh = (int)(((s % V) + V) % V);
+  const bool vec = ((uintptr_t)row % 16 == 0) && (P % V == 0) && s >= 0 && s + cnt <= P;
+  if (vec) {
+    const T* src = row + (s - sh);
+    const int nv = (sh + cnt + V - 1) / V;
+    for (int i = tid; i < nv; i += nt) cp_async16(dst + i * V, src + i * V);
+  } else {
+    for (int i = tid; i < cnt; i += nt) {
+      int64_t gpos = (s + i) % P;
+      if (gpos < 0) gpos += P;
+      cp_async_small<(int)sizeof(T)>(dst + sh + i, row + gpos);
+    }
+  }
+  return sh;
+}
+
+// ---- analysis ----
+// One level: from the input A of this level (chunk + right halo r) the
+// low-pass outputs go to lo_dst, the details of the chunk to dl.
+template <typename T, int K>
+__device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half, int m,
+                                          const T* h, const T* g, int tid, int nt) {
+  using V2 = typename FVec2<T>::type;
+  const V2* A2 = reinterpret_cast<const V2*>(A);
+  if constexpr (K <= 4) {
+    // two neighbouring outputs j, j + 1 per thread share K/2 + 1 pair loads
+    for (int p = tid; 2 * p < m; p += nt) {
+      T v[K + 2];
+#pragma unroll
+      for (int t = 0; t <= K / 2; ++t) {
+        const V2 w = A2[2 * p + t];
+        v[2 * t] = w.x;
+        v[2 * t + 1] = w.y;
+      }
+      T lo0 = T(0), hi0 = T(0), lo1 = T(0), hi1 = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        lo0 = fma(h[k], v[k], lo0);
+        hi0 = fma(g[k], v[k], hi0);
+        lo1 = fma(h[k], v[k + 2], lo1);
+        hi1 = fma(g[k], v[k + 2], hi1);
+      }
+      const int j = 2 * p;
+      lo_dst[j] = lo0;
+      if (j + 1 < m) lo_dst[j + 1] = lo1;
+      if (j < half) dl[j] = hi0;
+      if (j + 1 < half) dl[j + 1] = hi1;
+    }
+  } else {
+    // longer filters: one output per thread, neighbouring threads read
+    // neighbouring pairs (no bank conflicts)
+    for (int j = tid; j < m; j += nt) {
+      T lo = T(0), hi = T(0);
+#pragma unroll
+      for (int t = 0; t < K / 2; ++t) {
+        const V2 w = A2[j + t];
+        lo = fma(h[2 * t], w.x, lo);
+        lo = fma(h[2 * t + 1], w.y, lo);
+        hi = fma(g[2 * t], w.x, hi);
+        hi = fma(g[2 * t + 1], w.y, hi);
+      }
+      lo_dst[j] = lo;
+      if (j < half) dl[j] = hi;
+    }
+  }
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_filter_dwt(const FilterArgs a) {
+__global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.levels;
   T* A = reinterpret_cast<T*>(smem_raw);
-  T* B = A + kFBuf;
+  T* B = A + fdwt_cap_a<T, K>(L);
   T h[K], g[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     h[k] = (T)a.h[k];
     g[k] = (T)a.g[k];
   }
-  const int64_t row = blockIdx.x / a.chunks, k0 = (blockIdx.x - row * a.chunks) * kFChunk;
+  const unsigned chunks = (unsigned)a.chunks;
+  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kFChunk;
   const int64_t n = a.n;
-  const int L = a.levels;
   const int C = (int)min((int64_t)kFChunk, n - k0);
-  const T* x = static_cast<const T*>(a.in) + row * n;
   T* out = static_cast<T*>(a.out) + row * n;
-  int r = (K - 2) * ((1 << L) - 1);  // right halo of the current level
-  for (int i = threadIdx.x; i < C + r; i += blockDim.x) A[i] = x[fwrap(k0 + i, n)];
+  // the chunk and the (K - 2)(2^L - 1) samples to its right that the coarser
+  // levels' filters reach; k0 is a multiple of 16 bytes, so no shift
+  int r = (K - 2) * ((1 << L) - 1);
+  stage(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x, blockDim.x);
+  cp_async_wait_all();
   __syncthreads();
-  int len = C;  // chunk length at the current level
-  for (int l = 1; l <= L; ++l) {
-    const int rn = (r - (K - 2)) / 2;  // halo of the next level
-    const int m = len / 2 + rn;        // outputs of this level (chunk + halo)
-    T* dl = out + (n >> l) + (k0 >> l);
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      T lo = T(0), hi = T(0);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const T v = A[2 * j + k];
-        lo = fma(h[k], v, lo);
-        hi = fma(g[k], v, hi);
-      }
-      B[j] = lo;
-      if (j < len / 2) dl[j] = hi;
-    }
+  int len = C, l = 1;
+  // fine levels: the whole block
+  for (; l <= L && (len >> 1) > 64; ++l) {
+    const int rn = (r - (K - 2)) / 2;  // right halo of the next level
+    const int half = len / 2;
+    dwt_level<T, K>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half, half + rn,
+                    h, g, threadIdx.x, blockDim.x);
     __syncthreads();
     T* t = A;
     A = B;
     B = t;
-    len /= 2;
+    len = half;
     r = rn;
   }
-  for (int i = threadIdx.x; i < len; i += blockDim.x) out[(k0 >> L) + i] = A[i];
+  // coarse levels (at most 64 low-pass outputs of the chunk): warp 0 alone
+  if (l <= L && threadIdx.x < 32) {
+    for (; l <= L; ++l) {
+      const int rn = (r - (K - 2)) / 2;
+      const int half = len / 2;
+      dwt_level<T, K>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half,
+                      half + rn, h, g, threadIdx.x, 32);
+      __syncwarp();
+      T* t = A;
+      A = B;
+      B = t;
+      len = half;
+      r = rn;
+    }
+  }
+}
+
+// ---- synthesis ----
+// window of level l: [lo(l), (m0 + C) >> l) with lo(l) = floor(lo(l-1) / 2) - HL,
+// lo(0) = m0.  As m0 is a multiple of 2^12, lo(l) = (m0 >> l) - e_l with
+// e_0 = 0, e_l = ceil(e_{l-1} / 2) + HL, the same for every chunk.
+//
+// One level l >= 2: pairs (2q, 2q+1) of level l-1, q = q0 + i, from a_l[q - t]
+// and d_l[q - t] (t < K/2), found at window index HL + i - t, written to B;
+// two pairs per thread share their loads.
+template <typename T, int K>
+__device__ __forceinline__ void idwt_level(const T* Acur, const T* D, T* B, int np, int j00,
+                                           const T* h, const T* g, int tid, int nt) {
+  constexpr int HL = K / 2 - 1;
+  for (int p = tid; 2 * p < np; p += nt) {
+    const int b1 = HL + 2 * p + 1;  // window index of the second pair
+    T av[K / 2 + 1], dv[K / 2 + 1];
+#pragma unroll
+    for (int i = 0; i <= K / 2; ++i) {
+      av[i] = Acur[b1 - i];
+      dv[i] = D[b1 - i];
+    }
+    T e0 = T(0), o0 = T(0), e1 = T(0), o1 = T(0);
+#pragma unroll
+    for (int t = 0; t < K / 2; ++t) {
+      e1 = fma(h[2 * t], av[t], e1);
+      e1 = fma(g[2 * t], dv[t], e1);
+      o1 = fma(h[2 * t + 1], av[t], o1);
+      o1 = fma(g[2 * t + 1], dv[t], o1);
+      e0 = fma(h[2 * t], av[t + 1], e0);
+      e0 = fma(g[2 * t], dv[t + 1], e0);
+      o0 = fma(h[2 * t + 1], av[t + 1], o0);
+      o0 = fma(g[2 * t + 1], dv[t + 1], o0);
+    }
+    const int j = j00 + 4 * p;
+    if (j >= 0) B[j] = e0;
+    B[j + 1] = o0;
+    if (2 * p + 1 < np) {
+      B[j + 2] = e1;
+      B[j + 3] = o1;
+    }
+  }
+}
+
+template <typename T> struct FVec16;
+template <> struct FVec16<float> { using type = float4; };
+template <> struct FVec16<double> { using type = double2; };
+
+// Level 1, the largest: a thread makes 4 pairs (8 output samples).  The
+// window start of both a_1 and d_1 is lo(1) = m0/2 - HL, so their shifts in
+// the 16-byte aligned buffers are compile-time constants: 0 for a_1 written
+// by level 2, (-HL) mod V for a staged window.  Eight values of each from
+// aligned 16-byte loads cover the HL + 4 that 4 pairs need.
+template <typename T, int K, bool A_STAGED>
+__device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, bool v16_ok, int np,
+                                            const T* h, const T* g, int tid, int nt) {
+  using VT = typename FVec16<T>::type;
+  constexpr int V = fvec<T>();
+  constexpr int HL = K / 2 - 1;
+  constexpr int SD = (-HL) & (V - 1);  // shift of a staged level-1 window
+  constexpr int SA = A_STAGED ? SD : 0;
+  for (int p = tid; 4 * p < np; p += nt) {
+    T ra[8], rd[8];
+#pragma unroll
+    for (int i = 0; i < 8 / V; ++i) {
+      *reinterpret_cast<VT*>(ra + i * V) = reinterpret_cast<const VT*>(A1 + 4 * p)[i];
+      *reinterpret_cast<VT*>(rd + i * V) = reinterpret_cast<const VT*>(D1 + 4 * p)[i];
+    }
+    T y[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T e = T(0), o = T(0);
+#pragma unroll
+      for (int t = 0; t < K / 2; ++t) {
+        const T av = ra[HL + k - t + SA], dv = rd[HL + k - t + SD];
+        e = fma(h[2 * t], av, e);
+        e = fma(g[2 * t], dv, e);
+        o = fma(h[2 * t + 1], av, o);
+        o = fma(g[2 * t + 1], dv, o);
+      }
+      y[2 * k] = e;
+      y[2 * k + 1] = o;
+    }
+    T* xp = xo + 8 * p;
+    if (v16_ok && 4 * p + 3 < np) {
+#pragma unroll
+      for (int i = 0; i < 8 / V; ++i) reinterpret_cast<VT*>(xp)[i] = *reinterpret_cast<VT*>(y + i * V);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (4 * p + k < np) {
+          xp[2 * k] = y[2 * k];
+          xp[2 * k + 1] = y[2 * k + 1];
+        }
+    }
+  }
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_filter_idwt(const FilterArgs a) {
+__global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   pdl_wait();
   pdl_trigger();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int V = fvec<T>();
   constexpr int HL = K / 2 - 1;  // extra coefficients needed on the left
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* B = A + kFChunk + 64;
-  T* D = B + kFChunk + 64;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.levels;
+  T* S = reinterpret_cast<T*>(smem_raw);
+  T* P0 = S + fidwt_stage_cap<T, K>(L);
+  T* P1 = P0 + fidwt_seg_cap<T, K>(1);
   T h[K], g[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     h[k] = (T)a.h[k];
     g[k] = (T)a.g[k];
   }
-  const int64_t row = blockIdx.x / a.chunks, m0 = (blockIdx.x - row * a.chunks) * kFChunk;
+  const unsigned chunks = (unsigned)a.chunks;
+  const int64_t row = blockIdx.x / chunks, m0 = (int64_t)(blockIdx.x % chunks) * kFChunk;
   const int64_t n = a.n;
-  const int L = a.levels;
   const int C = (int)min((int64_t)kFChunk, n - m0);
+  const int64_t end = m0 + C;
   const T* c = static_cast<const T*>(a.in) + row * n;
   T* x = static_cast<T*>(a.out) + row * n;
-  // lo_[l]: first index needed at level l (relative origin of the buffers)
-  int64_t lo_[kFMaxLevels + 1];
-  lo_[0] = m0;
-  for (int l = 1; l <= L; ++l) {
-    const int64_t p = lo_[l - 1];
-    lo_[l] = (p >= 0 ? p / 2 : -((-p + 1) / 2)) - HL;  // floor(p / 2) - HL
-  }
-  const int64_t nL = n >> L;
-  const int lenL = (int)(((m0 + C) >> L) - lo_[L]);
-  for (int i = threadIdx.x; i < lenL; i += blockDim.x) A[i] = c[fwrap(lo_[L] + i, nL)];
-  for (int l = L; l >= 1; --l) {
-    const int64_t nl = n >> l;
-    const int len_l = (int)(((m0 + C) >> l) - lo_[l]);
-    const T* dl = c + nl;  // d_l occupies [n >> l, n >> (l - 1))
-    for (int i = threadIdx.x; i < len_l; i += blockDim.x) D[i] = dl[fwrap(lo_[l] + i, nl)];
-    __syncthreads();
-    const int len_o = (int)(((m0 + C) >> (l - 1)) - lo_[l - 1]);
-    for (int i = threadIdx.x; i < len_o; i += blockDim.x) {
-      const int64_t j = lo_[l - 1] + i;
-      const int64_t q = j >= 0 ? j / 2 : -((-j + 1) / 2);  // floor(j / 2)
-      const int p = (int)(j - 2 * q);
-      T v = T(0);
-#pragma unroll
-      for (int t = 0; t < K / 2; ++t) {
-        const int s = (int)(q - t - lo_[l]);
-        v = fma(h[p + 2 * t], A[s], v);
-        v = fma(g[p + 2 * t], D[s], v);
+  auto e_of = [](int l) {  // e_l of the window start lo(l) = (m0 >> l) - e_l
+    int e = 0;
+    for (int i = 0; i < l; ++i) e = (e + 1) / 2 + HL;
+    return e;
+  };
+  // stage the windows a_L, d_L, ..., d_1: window w by warp w mod 8 (each
+  // warp sets up only its own windows), then one wait for everything
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    int off = 0;
+    for (int w = 0; w <= L; ++w) {
+      const int l = w == 0 ? L : L + 1 - w;
+      if (w % nwarps == warp) {
+        const int64_t nl = n >> l, s = (m0 >> l) - e_of(l);
+        stage(S + off, w == 0 ? c : c + nl, nl, s, (int)((end >> l) - s), lane, 32);
       }
-      B[i] = v;
+      off += fidwt_seg_cap<T, K>(l);
+    }
+  }
+  __shared__ int s_e[kFMaxLevels + 1];
+  if (threadIdx.x <= (unsigned)L) s_e[threadIdx.x] = e_of(threadIdx.x);
+  cp_async_wait_all();
+  __syncthreads();
+  // With m0 a multiple of 2^12, everything a level needs is a small integer:
+  //   shift of the window in its buffer  (-e_l) mod V    ((m0 >> l) = 0 mod V)
+  //   pairs of level l-1                 np  = (C >> l) + ceil(e_{l-1} / 2)
+  //   first output in the window         j00 = -(e_{l-1} mod 2)
+  const T* Acur = S + ((-s_e[L]) & (V - 1));
+  int doff = fidwt_seg_cap<T, K>(L);
+  int l = L;
+  // coarse levels >= 2 (at most 64 pairs of the chunk): warp 0 alone
+  if (l >= 2 && (C >> l) <= 64) {
+    if (threadIdx.x < 32) {
+      const T* A2 = Acur;
+      int doff2 = doff;
+      for (int l2 = l; l2 >= 2 && (C >> l2) <= 64; --l2) {
+        const int em = s_e[l2 - 1];
+        const T* D = S + doff2 + ((-s_e[l2]) & (V - 1));
+        doff2 += fidwt_seg_cap<T, K>(l2);
+        T* B = ((L - l2) & 1) ? P1 : P0;
+        idwt_level<T, K>(A2, D, B, (C >> l2) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x, 32);
+        __syncwarp();
+        A2 = B;
+      }
+    }
+    // every thread advances to the first fine level
+    for (; l >= 2 && (C >> l) <= 64; --l) {
+      doff += fidwt_seg_cap<T, K>(l);
+      Acur = ((L - l) & 1) ? P1 : P0;
     }
     __syncthreads();
-    T* tt = A;
-    A = B;
-    B = tt;
   }
-  for (int i = threadIdx.x; i < C; i += blockDim.x) x[m0 + i] = A[i];
+  // fine levels >= 2: the whole block
+  for (; l >= 2; --l) {
+    const int em = s_e[l - 1];
+    const T* D = S + doff + ((-s_e[l]) & (V - 1));
+    doff += fidwt_seg_cap<T, K>(l);
+    T* B = ((L - l) & 1) ? P1 : P0;
+    idwt_level<T, K>(Acur, D, B, (C >> l) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x,
+                     blockDim.x);
+    __syncthreads();
+    Acur = B;
+  }
+  // level 1: C/2 pairs, straight to the output (doff is the d_1 window)
+  const bool v16_ok = (uintptr_t)(x + m0) % 16 == 0;
+  if (L == 1)
+    idwt_level1<T, K, true>(S, S + doff, x + m0, v16_ok, C >> 1, h, g, threadIdx.x, blockDim.x);
+  else
+    idwt_level1<T, K, false>(Acur, S + doff, x + m0, v16_ok, C >> 1, h, g, threadIdx.x,
+                             blockDim.x);
 }
 
 template <typename T, int K>
-cudaError_t filter_launch_k(bool fwd, const FilterArgs& a, unsigned grid, cudaStream_t s) {
-  const size_t smem = fwd ? 2 * (size_t)kFBuf * sizeof(T) : 3 * (size_t)(kFChunk + 64) * sizeof(T);
+size_t filter_smem(bool fwd, int L) {
+  const int elems = fwd ? fdwt_cap_a<T, K>(L) + fdwt_cap_b<T, K>(L)
+                        : fidwt_stage_cap<T, K>(L) + 2 * fidwt_seg_cap<T, K>(1);
+  return (size_t)elems * sizeof(T);
+}
+
+template <typename T, int K>
+cudaError_t filter_launch_k(bool fwd, const FilterArgs& a, int64_t total, cudaStream_t s) {
+  const size_t smem = filter_smem<T, K>(fwd, a.levels);
+  auto kern = fwd ? k_filter_dwt<T, K> : k_filter_idwt<T, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
+  cfg.gridDim = dim3((unsigned)total);
+  cfg.blockDim = dim3(kFThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -165,27 +438,20 @@ cudaError_t filter_launch_k(bool fwd, const FilterArgs& a, unsigned grid, cudaSt
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (fwd) {
-    cudaError_t e = cudaFuncSetAttribute(k_filter_dwt<T, K>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, k_filter_dwt<T, K>, a);
-  }
-  cudaError_t e = cudaFuncSetAttribute(k_filter_idwt<T, K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, k_filter_idwt<T, K>, a);
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <typename T>
 cudaError_t filter_launch(bool fwd, FilterArgs a, int K, cudaStream_t s) {
   a.chunks = (a.n + kFChunk - 1) / kFChunk;
-  const int64_t g = a.rows * a.chunks;
-  if (g == 0) return cudaSuccess;
-  if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int64_t total = a.rows * a.chunks;
+  if (total == 0) return cudaSuccess;
+  if (total > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   switch (K) {
-    case 2: return filter_launch_k<T, 2>(fwd, a, (unsigned)g, s);
-    case 4: return filter_launch_k<T, 4>(fwd, a, (unsigned)g, s);
-    case 6: return filter_launch_k<T, 6>(fwd, a, (unsigned)g, s);
-    case 8: return filter_launch_k<T, 8>(fwd, a, (unsigned)g, s);
+    case 2: return filter_launch_k<T, 2>(fwd, a, total, s);
+    case 4: return filter_launch_k<T, 4>(fwd, a, total, s);
+    case 6: return filter_launch_k<T, 6>(fwd, a, total, s);
+    case 8: return filter_launch_k<T, 8>(fwd, a, total, s);
   }
   return cudaErrorInvalidValue;
 }
