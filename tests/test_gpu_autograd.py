@@ -75,7 +75,7 @@ def test_loss_and_gradient_match_oracle_fp32(fused):
     xn = x.detach().double().cpu().numpy()
     ref_loss, _, _ = oracle.denoise_loss(xn, 3, 0.05, 1e-3)
     ref_g = oracle.denoise_loss_grad(xn, 3, 0.05, 1e-3)
-    assert abs(float(loss) - ref_loss) <= 1e-5 * abs(ref_loss)
+    assert abs(float(loss.detach()) - ref_loss) <= 1e-5 * abs(ref_loss)
     assert oracle.rel_l2(x.grad.double().cpu().numpy(), ref_g) <= 1e-5
 
 
@@ -101,7 +101,7 @@ def test_gradient_workload_full_size():
     loss.backward()
     xn = x.detach().double().cpu().numpy()
     ref_loss, _, _ = oracle.denoise_loss(xn, cfg.levels, cfg.threshold, cfg.l1_weight)
-    assert abs(float(loss) - ref_loss) <= 1e-5 * abs(ref_loss)
+    assert abs(float(loss.detach()) - ref_loss) <= 1e-5 * abs(ref_loss)
     ref_g = oracle.denoise_loss_grad(xn, cfg.levels, cfg.threshold, cfg.l1_weight)
     assert oracle.rel_l2(x.grad.double().cpu().numpy(), ref_g) <= 1e-5
 
