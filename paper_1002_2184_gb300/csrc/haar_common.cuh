@@ -209,11 +209,29 @@ __device__ __forceinline__ void store2(__half* p, const float v[2]) {
 }
 
 // accumulators -> 8 consecutive elements.
+// Eight fp32 values: when the address allows it, one 32-byte store (a whole
+// sector, Blackwell's 256-bit st), so no sector is written in two halves by
+// two instructions; else two 16-byte stores.
 __device__ __forceinline__ void store8(float* p, const float v[8]) {
+  if (((uintptr_t)p & 31) == 0) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]),
+                 "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+    return;
+  }
   store4(p, v);
   store4(p + 4, v + 4);
 }
 __device__ __forceinline__ void store8(double* p, const double v[8]) {
+  if (((uintptr_t)p & 31) == 0) {  // two whole sectors
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+                 "d"(v[2]), "d"(v[3])
+                 : "memory");
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 4), "d"(v[4]), "d"(v[5]),
+                 "d"(v[6]), "d"(v[7])
+                 : "memory");
+    return;
+  }
   store4(p, v);
   store4(p + 4, v + 4);
 }

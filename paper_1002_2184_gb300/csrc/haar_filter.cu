@@ -306,8 +306,7 @@ __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, boo
     }
     T* xp = xo + 8 * p;
     if (v16_ok && 4 * p + 3 < np) {
-#pragma unroll
-      for (int i = 0; i < 8 / V; ++i) reinterpret_cast<VT*>(xp)[i] = *reinterpret_cast<VT*>(y + i * V);
+      store8(xp, y);  // whole sectors where the address allows
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k)
