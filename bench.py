@@ -395,11 +395,33 @@ def e2e_ours(api, synth, dev, cfg, steps, world):
     el_ms = (time.perf_counter() - t0) * 1e3
     ms, units = aggregate(el_ms, float(H * W) * steps, world, dev)
     ok = all(bool(torch.allclose(h, host_in, atol=1e-5)) for h in host_out)
+
+    # the host link alone: the same uploads and downloads, overlapped the
+    # same way, with no transform in between (the ceiling for this metric)
+    def link(n):
+        for k in range(n):
+            i = k % 2
+            with torch.cuda.stream(s_up):
+                x[i].copy_(host_in, non_blocking=True)
+            with torch.cuda.stream(s_dn):
+                host_out[i].copy_(y[i], non_blocking=True)
+
+    link(4)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    link(steps)
+    torch.cuda.synchronize(dev)
+    link_ms = (time.perf_counter() - t0) * 1e3 / steps
+    step_ms = el_ms / steps
     return {"value": round(units / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": H * W * 4, "d2h_bytes_per_step": H * W * 4,
             "steps": steps, "round_trip_ok": ok,
+            "ms_per_step": round(step_ms, 4),
+            "link_only_ms_per_step": round(link_ms, 4),
+            "frac_of_link": round(link_ms / step_ms, 4),
             "timing": "host wall clock from the first upload to the last download, "
-                      "device synchronised at both ends"}
+                      "device synchronised at both ends; link_only = the same copies "
+                      "without the transforms"}
 
 
 def cpu_baseline_oracle(synth, cfg, min_seconds=10.0):
