@@ -659,10 +659,10 @@ def filter_form(api, synth, dev):
 
 
 def volume_form(api, synth, dev):
-    """3D: a 256^3 fp32 volume (slices of the image generator), 3 levels,
-    DWT + IDWT round trip."""
+    """3D: a 512^3 fp32 volume (slices of the image generator; 512 MiB, larger
+    than L2), 3 levels, DWT + IDWT round trip."""
     import torch
-    side, L = 256, 3
+    side, L = 512, 3
     sl = [torch.from_numpy(synth.piecewise_smooth_image(side, side, 77, i).astype(np.float32))
           for i in range(8)]
     x = torch.stack([sl[i % 8] for i in range(side)]).to(dev)

@@ -15,6 +15,8 @@
 // Transforms deeper than three levels chain launches through a workspace.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fasthaar.h"
 #include "haar_internal.h"
 #include "haar_kernels.cuh"
@@ -35,6 +37,7 @@ struct Pass3 {
   int levels;
   int64_t batch, d, h, w;
   int64_t tz, ty, tx, ntiles;
+  int vec4;  // fp32 throughout, 16-byte aligned bases and strides, w % 32 == 0
 };
 
 // 3D butterfly on v[z][y][x]; o[bz][by][bx].
@@ -99,6 +102,56 @@ __device__ __forceinline__ Oct classify3(int i, int j, int k, int D1, int H1, in
   o.j = j;
   o.k = k;
   return o;
+}
+
+// The coefficients of levels 2..L and LLL_L that a full 8 x 8 x 64 tile
+// exchanges with its tile-local low-band layout are exactly 128 aligned runs
+// of four values (L <= 3): for L = 1 the 4 x 4 x 32 LLL_1; else 7 octants x
+// 2 x 2 rows x 4 runs of level 2, then 7 x 2 runs of level 3 and 2 of LLL_3
+// (L = 3) or 2 x 2 x 4 runs of LLL_2 (L = 2).  Thread t moves run t.
+struct Run4 {
+  int g, bz, by, bx;  // level (0 = LLL_L) and octant
+  int i, j, k;        // position inside the octant, k a multiple of 4
+  int si, sj, sk;     // position in the tile-local layout
+};
+template <int L>
+__device__ __forceinline__ Run4 run4(int t) {
+  Run4 r{};
+  if constexpr (L == 1) {
+    r.i = t >> 5;
+    r.j = (t >> 3) & 3;
+    r.k = 4 * (t & 7);
+  } else {
+    if (t < 112) {
+      const int o = (t >> 4) + 1, row = (t >> 2) & 3;
+      r.g = 2;
+      r.bz = o >> 2;
+      r.by = (o >> 1) & 1;
+      r.bx = o & 1;
+      r.i = row >> 1;
+      r.j = row & 1;
+      r.k = 4 * (t & 3);
+    } else if (L == 2) {
+      const int u = t - 112, row = u >> 2;
+      r.i = row >> 1;
+      r.j = row & 1;
+      r.k = 4 * (u & 3);
+    } else if (t < 126) {
+      const int u = t - 112, o = (u >> 1) + 1;
+      r.g = 3;
+      r.bz = o >> 2;
+      r.by = (o >> 1) & 1;
+      r.bx = o & 1;
+      r.k = 4 * (u & 1);
+    } else {
+      r.k = 4 * (t - 126);
+    }
+  }
+  // octant extents in the layout of a full tile: 2 x 2 x 16 at level 2, 1 x 1 x 8 at 3
+  r.si = r.g == 2 ? 2 * r.bz + r.i : r.g == 3 ? r.bz + r.i : r.i;
+  r.sj = r.g == 2 ? 2 * r.by + r.j : r.g == 3 ? r.by + r.j : r.j;
+  r.sk = r.g == 2 ? 16 * r.bx + r.k : r.g == 3 ? 8 * r.bx + r.k : r.k;
+  return r;
 }
 
 template <typename Tin, typename Tout, int L>
@@ -191,6 +244,18 @@ __global__ void __launch_bounds__(kNT3) k_dwt3d(const Pass3 p) {
   }
 
   // ---- scatter the tile's low-band layout to the global octants ----
+  if constexpr (std::is_same<Tout, float>::value && std::is_same<A, float>::value) {
+    if (p.vec4 && vd == kTD && vh == kTH && vw == kTW) {
+      const Run4 r = run4<L>(tid);
+      const float4 v = *reinterpret_cast<const float4*>(&S[r.si][r.sj][r.sk]);
+      float* g = r.g ? dst + oct_off(p, p.d_zs, p.d_rs, r.g, r.bz, r.by, r.bx, (z0 >> r.g) + r.i,
+                                     (y0 >> r.g) + r.j, (x0 >> r.g) + r.k)
+                     : static_cast<float*>(p.ll) + b * p.l_bs + ((z0 >> L) + r.i) * p.l_zs +
+                           ((y0 >> L) + r.j) * p.l_rs + (x0 >> L) + r.k;
+      *reinterpret_cast<float4*>(g) = v;
+      return;
+    }
+  }
   const int n1 = D1 * H1 * W1;
   for (int idx = tid; idx < n1; idx += kNT3) {
     const int i = idx / (H1 * W1), rem = idx - i * H1 * W1, j = rem / W1, k = rem - j * W1;
@@ -243,7 +308,20 @@ __global__ void __launch_bounds__(kNT3) k_idwt3d(const Pass3 p) {
   }
   // ---- gather the deeper coefficients of the tile into shared memory ----
   const int D1 = vd >> 1, H1 = vh >> 1, W1 = vw >> 1;
-  const int n1 = D1 * H1 * W1;
+  bool gathered = false;
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<A, float>::value) {
+    if (p.vec4 && vd == kTD && vh == kTH && vw == kTW) {
+      const Run4 r = run4<L>(tid);
+      const float* g = r.g ? src + oct_off(p, p.s_zs, p.s_rs, r.g, r.bz, r.by, r.bx,
+                                           (z0 >> r.g) + r.i, (y0 >> r.g) + r.j, (x0 >> r.g) + r.k)
+                           : static_cast<const float*>(p.ll) + b * p.l_bs +
+                                 ((z0 >> L) + r.i) * p.l_zs + ((y0 >> L) + r.j) * p.l_rs +
+                                 (x0 >> L) + r.k;
+      *reinterpret_cast<float4*>(&S[r.si][r.sj][r.sk]) = __ldg(reinterpret_cast<const float4*>(g));
+      gathered = true;
+    }
+  }
+  const int n1 = gathered ? 0 : D1 * H1 * W1;
   for (int idx = tid; idx < n1; idx += kNT3) {
     const int i = idx / (H1 * W1), rem = idx - i * H1 * W1, j = rem / W1, k = rem - j * W1;
     const Oct oc = classify3(i, j, k, D1, H1, W1, L);
@@ -489,6 +567,13 @@ int run3(const haar_desc3* in, const haar_desc3* out, int levels, void* ws, size
       const int64_t d1 = in->d >> s1, h1 = in->h >> s1, w1 = in->w >> s1;
       p.ll = wsb + off[k + 1]; p.l_rs = w1; p.l_zs = h1 * w1; p.l_bs = d1 * h1 * w1;
       p.ll_acc = 1;
+    }
+    {
+      auto a16 = [](const void* ptr) { return (uintptr_t)ptr % 16 == 0; };
+      p.vec4 = ptin == HAAR_F32 && ptout == HAAR_F32 && wk % 32 == 0 && a16(p.src) &&
+               a16(p.dst) && a16(p.ll) && p.s_bs % 4 == 0 && p.s_zs % 4 == 0 &&
+               p.s_rs % 4 == 0 && p.d_bs % 4 == 0 && p.d_zs % 4 == 0 && p.d_rs % 4 == 0 &&
+               p.l_bs % 4 == 0 && p.l_zs % 4 == 0 && p.l_rs % 4 == 0;
     }
     const cudaError_t e = dispatch3d(fwd, ptin, ptout, p, st);
     if (e != cudaSuccess) {

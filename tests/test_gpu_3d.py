@@ -21,7 +21,8 @@ def volume(shape, seed, dtype=torch.float32):
 
 
 CASES = [((1, 8, 8, 64), 1), ((1, 8, 8, 64), 2), ((2, 16, 32, 64), 3), ((1, 24, 40, 72), 3),
-         ((1, 32, 32, 128), 5), ((3, 8, 16, 128), 3), ((1, 64, 64, 64), 6)]
+         ((1, 32, 32, 128), 5), ((3, 8, 16, 128), 3), ((1, 64, 64, 64), 6),
+         ((1, 16, 24, 96), 3), ((2, 8, 8, 64), 3)]  # full and partial tiles mixed; batch
 
 
 @pytest.mark.parametrize("shape,levels", CASES)
