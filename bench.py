@@ -553,15 +553,22 @@ def grad_form(api, synth, dev):
     x = torch.stack([imgs[i % 8] for i in range(B * C)]).reshape(gc_.shape).to(dev)
     px = x.numel()
     L, t, lam = gc_.levels, gc_.threshold, gc_.l1_weight
-    plan = ad.DenoisePlan(x, L, t, lam)
-    plan.forward()
-    plan.backward()
+    # four input sets (4 x (x + grad) = 800 MB > L2) rotate inside the graph,
+    # so each step's forward reads its batch from DRAM; the backward re-reads
+    # the same batch right after, as a training step would
+    sets = 4
+    xs = [x] + [x.roll(k, dims=0).contiguous() for k in range(1, sets)]
+    plans = [ad.DenoisePlan(xk, L, t, lam) for xk in xs]
+    for pl in plans:
+        pl.forward()
+        pl.backward()
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        plan.forward()
-        plan.backward()
-    ms_graph = time_ms(g.replay, 50)
+        for pl in plans:
+            pl.forward()
+            pl.backward()
+    ms_graph = time_ms(g.replay, 20) / sets
 
     xr = x.clone().requires_grad_(True)
 
@@ -583,6 +590,7 @@ def grad_form(api, synth, dev):
     hbm = (peaks or {}).get("hbm_gbs") or 6800.0
     gbs = 12.0 * px / (ms_graph * 1e-3) / 1e9
     return {"workload": f"{B}x{C}x{H}x{W} fp32, {L} levels, soft threshold {t}, L1 weight {lam}",
+            "l2": f"{sets} rotating input sets in one graph (per-step time = replay / {sets})",
             "fused_graph_ms": round(ms_graph, 4),
             "fused_graph_gsamples_s": round(px / (ms_graph * 1e-3) / 1e9, 2),
             "fused_hbm_gbs": round(gbs, 1), "fused_frac_of_hbm": round(gbs / hbm, 4),

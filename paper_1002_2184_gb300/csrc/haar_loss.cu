@@ -24,21 +24,31 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   return v;
 }
-// Sum over the block of one value per thread, added once into *out: warp
-// shuffles, then one shared-memory slot per warp, then one atomic per block
-// (atomics from every warp to one address would serialise).  Every thread of
-// the block must call it.
-__device__ __forceinline__ void block_sum_to(double v, double* out) {
-  __shared__ double part[32];
-  v = warp_sum(v);
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+// Sum over the block of one value per thread, added once into *out (FP64):
+// warp shuffles and one shared-memory slot per warp in the value's own type,
+// then one conversion and one FP64 atomic per block (atomics from every warp
+// to one address would serialise).  FP64 arithmetic is a slow pipe on this
+// GPU, so it stays out of the per-thread work; an fp32 block partial is a
+// tree sum of at most 8192 terms (40 roundings deep).  Every thread of the
+// block must call it.
+template <typename T>
+__device__ __forceinline__ void block_sum_to(T v, double* out) {
+  __shared__ T part[32];
+  v = warp_sum_t(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) part[warp] = v;
   __syncthreads();
   if (warp == 0) {
     const int nw = (blockDim.x + 31) >> 5;
-    double t = lane < nw ? part[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) atomicAdd(out, t);
+    T t = lane < nw ? part[lane] : T(0);
+    t = warp_sum_t(t);
+    if (lane == 0) atomicAdd(out, (double)t);
   }
   __syncthreads();
 }
@@ -163,21 +173,29 @@ __global__ void __launch_bounds__(256) k_sqdiff_bwd(const T* __restrict__ a,
 //   d loss / d x  = W^T q,   q = [|c| > t] * lam' * sign(c) * [detail]
 //                              + [|c| <= t] * (2 g / n) * c,   lam' = lam g / n_d
 // (g: upstream gradient; n pixels, n_d detail coefficients).  Neither s nor
-// r has to be stored: the forward reads x and produces only the loss sums,
-// the backward reads x and writes the gradient.  Each is one kernel in which
-// a warp takes its 32 x 32 block through the analysis (registers and
-// shuffles, as dwt_block32), maps every coefficient in place, and runs the
-// synthesis back in registers (each lane holds every coarse coefficient on
-// its own path after the shuffles).
+// r has to be stored: the forward reads x and produces only the loss sums
+// (with |r|^2 = |clamp(c, -t, t)|^2 it needs no synthesis), the backward
+// reads x and writes the gradient.  Each is one kernel in which a warp takes
+// its 32 x 32 block through the analysis (registers and shuffles, as
+// dwt_block32) and maps every coefficient in place; the backward then runs
+// the synthesis back in registers (each lane holds every coarse coefficient
+// on its own path after the shuffles).
 // ---------------------------------------------------------------------------
-// Forward map: c -> -clamp(c, -t, t) = soft(c) - c; sums |soft(c)| over details.
+// Forward: since r = -W^T clamp(c, -t, t) and W is orthonormal, Parseval
+// gives |r|^2 = |clamp(c, -t, t)|^2, so the forward needs no synthesis: it
+// sums min(|c|, t)^2 over every coefficient and |soft(c)| = max(|c| - t, 0)
+// over the details, each coefficient once (the owner copy).
 template <typename T>
-struct OpResidual {
-  T t, l1;
+struct OpEnergy {
+  T t, l1, sq;
   __device__ __forceinline__ T operator()(T c, bool detail, bool owner) {
     const T a = fabs(c) - t;
-    if (detail && owner && a > T(0)) l1 += a;
-    return a > T(0) ? copysign(t, -c) : -c;
+    if (owner) {
+      if (detail && a > T(0)) l1 += a;
+      const T m = a > T(0) ? t : fabs(c);
+      sq += m * m;
+    }
+    return c;
   }
 };
 
@@ -199,8 +217,18 @@ struct DenoiseArgs {
   double* acc;       // forward sums: [0] = sum |s_detail|, [1] = sum r^2
   const void* g;     // upstream gradient (device scalar) or null (= 1)
   double t, k_scale, k_lam;  // threshold; 2/n; lam/n_d
+  float t_f, k_scale_f, k_lam_f;  // the same, rounded once on the host
   int levels;        // 1..5
 };
+
+// A parameter in the arithmetic type (fp32 kernels take the host-rounded
+// copies, so no thread converts from double).
+template <typename T>
+__device__ __forceinline__ T param(double d, float f);
+template <>
+__device__ __forceinline__ float param<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double param<double>(double d, float) { return d; }
 
 template <typename T>
 __device__ __forceinline__ T load_g(const void* g) {
@@ -228,22 +256,15 @@ __global__ void __launch_bounds__(256) k_denoise_loss(const DenoiseArgs a) {
   pdl_trigger();
   const int lane = threadIdx.x & 31;
   int64_t off, py, px;
-  OpResidual<T> op{(T)a.t, T(0)};
-  T sq = T(0);
+  OpEnergy<T> op{param<T>(a.t, a.t_f), T(0), T(0)};
   if (dn_block(a, off, py, px)) {  // warps outside the image contribute zeros
     const T* x = static_cast<const T*>(a.x) + off;
     WarpCoefs<T, L> k;
     warp_analysis<T, L>(x + py * a.w + px, a.w, lane, k);
     warp_map<T, L>(lane, k, op);
-    T r[4][8];
-    warp_synthesis<T, L>(lane, py, px, k, r);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) sq += r[i][j] * r[i][j];
   }
-  block_sum_to((double)op.l1, a.acc);
-  block_sum_to((double)sq, a.acc + 1);
+  block_sum_to(op.l1, a.acc);
+  block_sum_to(op.sq, a.acc + 1);
 }
 
 template <typename T, int L>
@@ -257,7 +278,8 @@ __global__ void __launch_bounds__(256) k_denoise_grad(const DenoiseArgs a) {
   const T* x = static_cast<const T*>(a.x) + off;
   WarpCoefs<T, L> k;
   warp_analysis<T, L>(x + py * a.w + px, a.w, lane, k);
-  OpGradient<T> op{(T)a.t, (T)a.k_scale * g, (T)a.k_lam * g};
+  OpGradient<T> op{param<T>(a.t, a.t_f), param<T>(a.k_scale, a.k_scale_f) * g,
+                   param<T>(a.k_lam, a.k_lam_f) * g};
   warp_map<T, L>(lane, k, op);
   T o[4][8];
   warp_synthesis<T, L>(lane, py, px, k, o);
@@ -464,6 +486,7 @@ int haar_denoise_forward(const haar_desc* x, int levels, double threshold, doubl
   a.w = x->w;
   a.acc = acc2;
   a.t = threshold;
+  a.t_f = (float)threshold;
   a.levels = levels;
   cudaError_t e = denoise_dispatch(x->dtype, false, a, st);
   if (e == cudaSuccess) {
@@ -498,6 +521,9 @@ int haar_denoise_backward(const haar_desc* x, const haar_desc* g_x, int levels, 
   a.t = threshold;
   a.k_scale = 2.0 / (double)n;
   a.k_lam = nd ? l1_weight / (double)nd : 0.0;
+  a.t_f = (float)a.t;
+  a.k_scale_f = (float)a.k_scale;
+  a.k_lam_f = (float)a.k_lam;
   a.levels = levels;
   return fail(denoise_dispatch(x->dtype, true, a, (cudaStream_t)cuda_stream));
 }
