@@ -1,0 +1,56 @@
+// haar_async.cuh -- asynchronous global -> shared staging with cp.async
+// (16-byte copies issued by every thread, one wait at the end) for the
+// kernels that work on a staged window of a row: the K-tap bank and the
+// undecimated transform.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fh {
+
+// elements per 16-byte copy
+template <typename T>
+__host__ __device__ constexpr int fvec() { return 16 / (int)sizeof(T); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Stage positions [s, s + cnt) of a sequence of period P stored at `row`
+// into dst[sh + i], sh = s mod (16 / sizeof(T)).  Inside the sequence and
+// with a 16-byte aligned row the copy is made of aligned 16-byte pieces
+// (which may also bring a few neighbours, inside [0, P)); otherwise, e.g. for
+// windows that wrap around, each element is copied on its own.  Returns sh.
+template <typename T>
+__device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s, int cnt, int tid,
+                                     int nt) {
+  constexpr int V = fvec<T>();
+  const int sh = (int)(((s % V) + V) % V);
+  const bool vec = ((uintptr_t)row % 16 == 0) && (P % V == 0) && s >= 0 && s + cnt <= P;
+  if (vec) {
+    const T* src = row + (s - sh);
+    const int nv = (sh + cnt + V - 1) / V;
+    for (int i = tid; i < nv; i += nt) cp_async16(dst + i * V, src + i * V);
+  } else {
+    for (int i = tid; i < cnt; i += nt) {
+      int64_t gpos = (s + i) % P;
+      if (gpos < 0) gpos += P;
+      cp_async_small<(int)sizeof(T)>(dst + sh + i, row + gpos);
+    }
+  }
+  return sh;
+}
+
+}  // namespace fh

@@ -13,10 +13,11 @@
 // row 0 = a_L, row l = d_l.  A block produces 2048 consecutive positions of
 // one row; the samples it needs (a halo of 2^L - 1 to the right for the
 // analysis, to the left for the synthesis) are staged in shared memory and
-// all levels are fused there.
+// all levels are fused there (staged with cp.async 16-byte copies).
 #include <cuda_runtime.h>
 
 #include "fasthaar.h"
+#include "haar_async.cuh"
 #include "haar_internal.h"
 #include "haar_kernels.cuh"
 
@@ -34,9 +35,10 @@ struct SwtArgs {
   int64_t chunks;
 };
 
-__device__ __forceinline__ int64_t wrap(int64_t k, int64_t n) {
-  k %= n;
-  return k < 0 ? k + n : k;
+// one staged window: the chunk and its halo, plus the 16-byte copy slack
+template <typename T>
+__host__ __device__ constexpr int swt_cap() {
+  return (kSwtChunk + kSwtHalo + 2 * fvec<T>() + fvec<T>() - 1) / fvec<T>() * fvec<T>();
 }
 
 template <typename T>
@@ -45,14 +47,16 @@ __global__ void __launch_bounds__(256) k_swt(const SwtArgs a) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
-  T* B = A + kSwtChunk + kSwtHalo;
-  const int64_t row = blockIdx.x / a.chunks, k0 = (blockIdx.x - row * a.chunks) * kSwtChunk;
+  T* B = A + swt_cap<T>();
+  const unsigned chunks = (unsigned)a.chunks;
+  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kSwtChunk;
   const int64_t n = a.n;
   const int C = (int)min((int64_t)kSwtChunk, n - k0);
   const int H = (1 << a.levels) - 1;
   const T* x = static_cast<const T*>(a.in) + row * n;
   T* out = static_cast<T*>(a.out) + row * (a.levels + 1) * n;
-  for (int i = threadIdx.x; i < C + H; i += blockDim.x) A[i] = x[wrap(k0 + i, n)];
+  stage(A, x, n, k0, C + H, threadIdx.x, blockDim.x);  // k0 is 16-byte aligned: no shift
+  cp_async_wait_all();
   __syncthreads();
   const T r = Consts<T>::s();
   for (int l = 1; l <= a.levels; ++l) {
@@ -77,22 +81,25 @@ __global__ void __launch_bounds__(256) k_iswt(const SwtArgs a) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* B = A + kSwtChunk + kSwtHalo;
-  T* D = B + kSwtChunk + kSwtHalo;
-  const int64_t row = blockIdx.x / a.chunks, k0 = (blockIdx.x - row * a.chunks) * kSwtChunk;
+  T* bufA = reinterpret_cast<T*>(smem_raw);
+  T* bufB = bufA + swt_cap<T>();
+  T* bufD = bufB + swt_cap<T>();
+  const unsigned chunks = (unsigned)a.chunks;
+  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kSwtChunk;
   const int64_t n = a.n;
   const int C = (int)min((int64_t)kSwtChunk, n - k0);
   const T* c = static_cast<const T*>(a.in) + row * (a.levels + 1) * n;
   T* x = static_cast<T*>(a.out) + row * n;
   const int L = a.levels;
   int H = (1 << L) - 1;  // left halo of a_L
-  for (int i = threadIdx.x; i < C + H; i += blockDim.x) A[i] = c[wrap(k0 - H + i, n)];
+  const T* A = bufA + stage(bufA, c, n, k0 - H, C + H, threadIdx.x, blockDim.x);
+  T* B = bufB;
   const T q = Consts<T>::s() * T(0.5);
   for (int l = L; l >= 1; --l) {
     const int s = 1 << (l - 1);
-    const T* dl = c + (int64_t)l * n;
-    for (int i = threadIdx.x; i < C + H; i += blockDim.x) D[i] = dl[wrap(k0 - H + i, n)];
+    const T* D = bufD + stage(bufD, c + (int64_t)l * n, n, k0 - H, C + H, threadIdx.x,
+                              blockDim.x);
+    cp_async_wait_all();
     __syncthreads();
     const int Hn = H - s;  // left halo of a_{l-1}
     for (int j = threadIdx.x; j < C + Hn; j += blockDim.x) {
@@ -100,9 +107,9 @@ __global__ void __launch_bounds__(256) k_iswt(const SwtArgs a) {
       B[j] = ((A[i] - D[i]) + (A[i - s] + D[i - s])) * q;
     }
     __syncthreads();
-    T* t = A;
+    T* next = B == bufB ? bufA : bufB;  // the buffer A came from
     A = B;
-    B = t;
+    B = next;
     H = Hn;
   }
   for (int i = threadIdx.x; i < C; i += blockDim.x) x[k0 + i] = A[i];
@@ -114,7 +121,7 @@ cudaError_t swt_launch(bool fwd, SwtArgs a, cudaStream_t s) {
   const int64_t g = a.rows * a.chunks;
   if (g == 0) return cudaSuccess;
   if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  const size_t smem = (size_t)(fwd ? 2 : 3) * (kSwtChunk + kSwtHalo) * sizeof(T);
+  const size_t smem = (size_t)(fwd ? 2 : 3) * swt_cap<T>() * sizeof(T);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g);
   cfg.blockDim = dim3(256);
