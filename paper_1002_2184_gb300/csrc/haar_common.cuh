@@ -44,6 +44,16 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned 
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 
+// A kernel parameter in the arithmetic type.  Parameters travel as double
+// plus a copy rounded to float once on the host, so that fp32 kernels never
+// convert from double per thread (FP64 is a slow pipe on this GPU).
+template <typename T>
+__device__ __forceinline__ T param(double d, float f);
+template <>
+__device__ __forceinline__ float param<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double param<double>(double d, float) { return d; }
+
 // ---------------------------------------------------------------------------
 // Accumulator type per storage type.
 // ---------------------------------------------------------------------------

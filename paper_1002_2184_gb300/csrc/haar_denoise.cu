@@ -24,6 +24,7 @@ __device__ __forceinline__ T shrink(T d, T t, bool hard) {
 struct ShrinkArgs {
   Pass p;  // src = x, dst = y (same geometry); batch, h, w, levels
   double t;
+  float t_f;  // t rounded once on the host
   int hard;
 };
 
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(256) k_denoise1d(const ShrinkArgs a) {
   const T* src = static_cast<const T*>(p.src) + b * p.s_bs + y * p.s_rs;
   T* dst = static_cast<T*>(p.dst) + b * p.d_bs + y * p.d_rs;
   const int64_t px = x0 + 8 * lane;
-  const T t = (T)a.t;
+  const T t = param<T>(a.t, a.t_f);
   const bool hard = a.hard != 0;
   T v[8];
   load8(src + px, v);
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) k_denoise2d(const ShrinkArgs a) {
   T* dst = static_cast<T*>(p.dst) + b * p.d_bs + py * p.d_rs + px;
   WarpCoefs<T, L> k;
   warp_analysis<T, L>(src + py * p.s_rs + px, p.s_rs, lane, k);
-  OpShrink<T> op{(T)a.t, a.hard != 0};
+  OpShrink<T> op{param<T>(a.t, a.t_f), a.hard != 0};
   warp_map<T, L>(lane, k, op);
   T o[4][8];
   warp_synthesis<T, L>(lane, py, px, k, o);
@@ -203,6 +204,7 @@ int shrink_entry(const haar_desc* x, const haar_desc* y, int levels, double thre
   a.p.h = x->h;
   a.p.w = x->w;
   a.t = threshold;
+  a.t_f = (float)threshold;
   a.hard = mode == HAAR_THRESH_HARD;
   const cudaError_t e = x->dtype == HAAR_F64
                             ? shrink_launch<double>(two_d, a, (cudaStream_t)stream)

@@ -40,6 +40,7 @@ struct FilterArgs {
   int levels;
   int64_t chunks;
   double h[kFMaxTaps], g[kFMaxTaps];
+  float hf[kFMaxTaps], gf[kFMaxTaps];  // the same, rounded once on the host
 };
 
 template <typename T> struct FVec2;
@@ -136,8 +137,8 @@ __global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
   T h[K], g[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    h[k] = (T)a.h[k];
-    g[k] = (T)a.g[k];
+    h[k] = param<T>(a.h[k], a.hf[k]);
+    g[k] = param<T>(a.g[k], a.gf[k]);
   }
   const unsigned chunks = (unsigned)a.chunks;
   const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kFChunk;
@@ -290,8 +291,8 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   T h[K], g[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    h[k] = (T)a.h[k];
-    g[k] = (T)a.g[k];
+    h[k] = param<T>(a.h[k], a.hf[k]);
+    g[k] = param<T>(a.g[k], a.gf[k]);
   }
   const unsigned chunks = (unsigned)a.chunks;
   const int64_t row = blockIdx.x / chunks, m0 = (int64_t)(blockIdx.x % chunks) * kFChunk;
@@ -440,6 +441,8 @@ int filter_entry(const void* in, void* out, int dtype, int64_t rows, int64_t n, 
   for (int k = 0; k < ntaps; ++k) {
     a.h[k] = lowpass[k];
     a.g[k] = ((k & 1) ? 1.0 : -1.0) * lowpass[ntaps - 1 - k];  // (-1)^(k+1) h[K-1-k]
+    a.hf[k] = (float)a.h[k];
+    a.gf[k] = (float)a.g[k];
   }
   const cudaError_t e = dtype == HAAR_F64 ? filter_launch<double>(fwd, a, ntaps, (cudaStream_t)stream)
                                           : filter_launch<float>(fwd, a, ntaps, (cudaStream_t)stream);

@@ -221,14 +221,6 @@ struct DenoiseArgs {
   int levels;        // 1..5
 };
 
-// A parameter in the arithmetic type (fp32 kernels take the host-rounded
-// copies, so no thread converts from double).
-template <typename T>
-__device__ __forceinline__ T param(double d, float f);
-template <>
-__device__ __forceinline__ float param<float>(double, float f) { return f; }
-template <>
-__device__ __forceinline__ double param<double>(double d, float) { return d; }
 
 template <typename T>
 __device__ __forceinline__ T load_g(const void* g) {
