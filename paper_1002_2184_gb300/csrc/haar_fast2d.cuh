@@ -352,16 +352,20 @@ __device__ __forceinline__ void idwt_block32(const Img2& im, int64_t y0, int64_t
   }
 }
 
+// One batch item of a pass.  A coefficient-typed low band is an output of
+// the analysis (Tout) but an input of the synthesis (Tin): the batch offset
+// is scaled by that type.
 template <typename Tin, typename Tout>
-__device__ __forceinline__ Img2 pass_image(const Pass& p, int64_t b) {
+__device__ __forceinline__ Img2 pass_image(const Pass& p, int64_t b, bool analysis) {
   using A = typename AccT<Tin>::type;
   Img2 im;
   im.src = static_cast<const Tin*>(p.src) + b * p.s_bs;
   im.s_rs = p.s_rs;
   im.dst = static_cast<Tout*>(p.dst) + b * p.d_bs;
   im.d_rs = p.d_rs;
-  im.ll = p.ll_acc ? (void*)(static_cast<A*>(p.ll) + b * p.l_bs)
-                   : (void*)(static_cast<Tout*>(p.ll) + b * p.l_bs);
+  im.ll = p.ll_acc   ? (void*)(static_cast<A*>(p.ll) + b * p.l_bs)
+          : analysis ? (void*)(static_cast<Tout*>(p.ll) + b * p.l_bs)
+                     : (void*)(const_cast<Tin*>(static_cast<const Tin*>(p.ll)) + b * p.l_bs);
   im.l_rs = p.l_rs;
   im.ll_acc = p.ll_acc;
   im.h = p.h;
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(256) k_dwt2d_fast(const Pass p) {
   const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
   const int64_t y0 = cy * (32 * WR) + (warp / WC) * 32;
   const int64_t x0 = cx * (32 * WC) + (warp % WC) * 32;
-  const Img2 im = pass_image<Tin, Tout>(p, b);
+  const Img2 im = pass_image<Tin, Tout>(p, b, true);
   A l5 = A(0);
   if (y0 < p.h && x0 < p.w) l5 = dwt_block32<Tin, Tout, L>(im, y0, x0, lane);
   if constexpr (L == 6) {
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(256, idwt_min_blocks<Tin>()) k_idwt2d_fast(con
   const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
   const int64_t y0 = cy * 32, x0 = cx * 256 + warp * 32;
   if (y0 >= p.h || x0 >= p.w) return;
-  idwt_block32<Tin, Tout, L>(pass_image<Tin, Tout>(p, b), y0, x0, lane);
+  idwt_block32<Tin, Tout, L>(pass_image<Tin, Tout>(p, b, false), y0, x0, lane);
 }
 
 template <typename Tin, typename Tout>

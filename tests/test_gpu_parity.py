@@ -117,6 +117,36 @@ def test_image_workload_full_size():
     assert oracle.rel_l2(host64(y), xn) <= 1e-6
 
 
+def test_precision_workload_full_size():
+    """64 x 2048 x 2048, 4 levels, through Plan (the benchmark's launch
+    configuration): bf16 storage, and uint8 input with bf16 coefficients and
+    fp32 output.  Three images spread over the batch are checked coefficient
+    by coefficient against the oracle (on exactly the values the GPU read);
+    the whole batch through its round-trip error."""
+    cfg = synth.PrecisionBatch()
+    distinct = 8  # the batch repeats 8 generated images, as the benchmark does
+    base = np.stack([synth.piecewise_smooth_image(cfg.h, cfg.w, cfg.seed, i)
+                     for i in range(distinct)])
+    xb = dev(base, torch.bfloat16).repeat(cfg.batch // distinct, 1, 1)
+    checked = (0, 37, cfg.batch - 1)
+    for x, cdt, ydt, tol in ((xb, torch.bfloat16, torch.bfloat16, 1e-2),
+                             ((xb.float().clamp(0, 1) * 255).round().to(torch.uint8),
+                              torch.bfloat16, torch.float32, 1e-2)):
+        c = torch.empty(x.shape, dtype=cdt, device=DEV)
+        y = torch.empty(x.shape, dtype=ydt, device=DEV)
+        plan = api.Plan(x, c, cfg.levels, y)
+        plan.dwt()
+        plan.idwt()
+        torch.cuda.synchronize()
+        for i in checked:
+            ref = oracle.dwt2d(host64(x[i]), cfg.levels)
+            assert_close(c[i], ref, cdt, f"precision dwt image {i} {x.dtype}")
+        xs = x.double()
+        err = float(torch.linalg.vector_norm(y.double() - xs) / torch.linalg.vector_norm(xs))
+        assert err <= tol, f"precision round trip {x.dtype}: {err:.3e}"
+        del c, y, plan
+
+
 @pytest.mark.parametrize("levels", [7, 12])
 def test_deep_2d_chained_passes(levels):
     x = dev(images(1, 4096, 4096, seed=levels), torch.float32)
@@ -140,6 +170,19 @@ def test_strided_and_offset_views():
         assert_close(c, oracle.dwt2d(host64(x), 4), torch.float32, f"strided off={off}")
         y = api.idwt2d(c, 4)
         assert oracle.rel_l2(host64(y), host64(x)) <= 1e-6
+
+
+@pytest.mark.parametrize("cdt", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("b,h,w,levels", [(3, 64, 256, 3), (4, 32, 64, 1), (2, 96, 160, 5)])
+def test_idwt2d_half_coefficients_to_fp32_batched(cdt, b, h, w, levels):
+    """Synthesis from 16-bit coefficients into fp32 output, several batch
+    items: every item's low band is read at its own offset."""
+    x = images(b, h, w, seed=b + h)
+    c = dev(oracle.dwt2d(x, levels), cdt)
+    y = api.idwt2d(c, levels, dtype=torch.float32)
+    assert y.dtype == torch.float32
+    ref = oracle.idwt2d(host64(c), levels)
+    assert_close(y, ref, torch.float32, f"idwt2d {cdt} -> fp32 {b}x{h}x{w} L{levels}")
 
 
 def test_uint8_input():
