@@ -190,3 +190,82 @@ def test_ragged_plan_geometry(lib):
     assert rc == 0
     assert lib.haar_dwt_2d_ragged(h0, None, 0, None, 0, None, 0, None) == 0  # nothing to do
     lib.haar_ragged_plan_destroy(h0)
+
+
+# ---------------------------------------------------------------------------
+# The other entry points: every case below is refused by the host-side
+# checks before anything is launched (fake device addresses, never touched).
+# ---------------------------------------------------------------------------
+def test_filter_bank_rejections(lib):
+    from paper_1002_2184_gb300 import _lib as L
+    h4 = (ctypes.c_double * 4)(0.48, 0.84, 0.22, -0.13)
+    for fn in (lib.haar_filter_dwt_1d, lib.haar_filter_idwt_1d):
+        assert fn(A, B, 2, 1, 64, 1, h4, 4, None) == L.HAAR_EDTYPE      # bf16: fp32/fp64 only
+        assert fn(A, B, 0, 1, 64, 0, h4, 4, None) == L.HAAR_EINVAL      # levels < 1
+        assert fn(A, B, 0, 1, 64, 11, h4, 4, None) == L.HAAR_EINVAL     # levels > 10
+        assert fn(A, B, 0, 1, 64, 1, h4, 3, None) == L.HAAR_EINVAL      # odd tap count
+        assert fn(A, B, 0, 1, 64, 1, None, 4, None) == L.HAAR_EINVAL    # no filter
+        assert fn(0, B, 0, 1, 64, 1, h4, 4, None) == L.HAAR_EINVAL      # null with data
+        assert fn(A, B, 0, 1, 96, 6, h4, 4, None) == L.HAAR_ESHAPE      # 96 % 64 != 0
+        assert fn(A, A + 64, 0, 2, 64, 1, h4, 4, None) == L.HAAR_EALIAS
+        assert fn(A, B, 0, 0, 64, 1, h4, 4, None) == L.HAAR_OK          # nothing to do
+
+
+def test_undecimated_rejections(lib):
+    from paper_1002_2184_gb300 import _lib as L
+    for fn in (lib.haar_swt_1d, lib.haar_iswt_1d):
+        assert fn(A, B, 3, 1, 64, 1, None) == L.HAAR_EDTYPE             # u8
+        assert fn(A, B, 0, 1, 64, 0, None) == L.HAAR_EINVAL
+        assert fn(A, B, 0, 1, 64, 11, None) == L.HAAR_EINVAL
+        assert fn(A, B, 0, 1, 8, 4, None) == L.HAAR_ESHAPE              # n < 2^levels
+        assert fn(0, B, 0, 1, 64, 1, None) == L.HAAR_EINVAL
+        assert fn(A, A + 64, 0, 1, 64, 1, None) == L.HAAR_EALIAS        # (L+1) rows overlap
+        assert fn(A, B, 0, 0, 64, 1, None) == L.HAAR_OK
+
+
+@pytest.mark.parametrize("name,two_d", [("haar_denoise_1d", False), ("haar_denoise_2d", True)])
+def test_shrinkage_rejections(lib, name, two_d):
+    from paper_1002_2184_gb300 import _lib as L
+    fn = getattr(lib, name)
+    h = 64 if two_d else 1
+    x, y = d(A, h=h, w=256), d(B, h=h, w=256)
+
+    def run(xd, yd, levels=2, t=0.1, mode=L.HAAR_THRESH_SOFT):
+        return fn(ctypes.byref(xd), ctypes.byref(yd), levels, ctypes.c_double(t), mode, None)
+
+    assert run(x, y, mode=7) == L.HAAR_EINVAL
+    assert run(x, y, t=-1.0) == L.HAAR_EINVAL
+    assert run(x, y, t=float("nan")) == L.HAAR_EINVAL
+    assert run(x, y, levels=0) == L.HAAR_EINVAL
+    assert run(x, y, levels=6 if two_d else 9) == L.HAAR_EINVAL       # beyond the fused depth
+    assert run(d(A, dt=2, h=h, w=256), d(B, dt=2, h=h, w=256)) == L.HAAR_EDTYPE
+    assert run(x, d(B, dt=4, h=h, w=256)) == L.HAAR_EDTYPE            # mixed dtypes
+    bad_w = 80 if two_d else 96  # 2D rows in multiples of 32, 1D in multiples of 256
+    assert run(d(A, h=h, w=bad_w), d(B, h=h, w=bad_w)) == L.HAAR_ESHAPE
+    assert run(x, d(A + 64, h=h, w=256)) == L.HAAR_EALIAS
+    assert run(d(A, b=0, h=h, w=256), d(B, b=0, h=h, w=256)) == L.HAAR_OK
+
+
+def test_volume_rejections(lib):
+    from paper_1002_2184_gb300 import _lib as L
+
+    def v(ptr, dt=0, b=1, dd=16, h=16, w=64, bs=None, zs=None, rs=None):
+        rs = w if rs is None else rs
+        zs = h * rs if zs is None else zs
+        bs = dd * zs if bs is None else bs
+        return L.HaarDesc3(ptr, dt, 0, b, dd, h, w, bs, zs, rs)
+
+    def run(fn, s, t, levels):
+        return fn(ctypes.byref(s), ctypes.byref(t), levels, None, 0, None)
+
+    for fn in (lib.haar_dwt_3d, lib.haar_idwt_3d):
+        assert run(fn, v(A), v(B), 0) == L.HAAR_EINVAL
+        assert run(fn, v(A), v(B), 31) == L.HAAR_EINVAL
+        assert run(fn, v(A, dd=12), v(B, dd=12), 3) == L.HAAR_ESHAPE     # depth % 8
+        assert run(fn, v(A), v(B, w=32), 1) == L.HAAR_EINVAL             # shapes differ
+        assert run(fn, v(A, dt=4), v(B, dt=0), 1) == L.HAAR_EDTYPE       # fp64 only with fp64
+        assert run(fn, v(A), v(A + 256), 1) == L.HAAR_EALIAS
+        assert run(fn, v(0), v(B), 1) == L.HAAR_EINVAL
+        assert run(fn, v(A, rs=32), v(B), 1) == L.HAAR_EINVAL            # row stride < w
+        assert run(fn, v(A), v(B), 4) == L.HAAR_EWORKSPACE               # deep: needs scratch
+        assert run(fn, v(A, b=0), v(B, b=0), 2) == L.HAAR_OK
