@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows-once", action="store_true",
+                    help="run the main operation of every row once on a case larger than L2 "
+                         "(for a profiler capture) and exit; prints no JSON line")
     return ap.parse_args()
 
 
@@ -767,6 +770,58 @@ def ragged_form(api, synth, dev, dense_fp32_gsamples):
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
+def rows_once():
+    """Each row's main operation once, on cases larger than L2, for an ncu
+    capture of the kernels behind every row: the ragged batch (first 64
+    images of the ragged shape list), the fused loss (32 x 3 x 512^2), 1D
+    signals (64 x 2^20: 8-level DWT + IDWT, shrinkage, one undecimated level,
+    Daubechies-4 bank), 2D shrinkage (4 x 4096^2), bf16 2D (64 x 2048^2,
+    4 levels) and a 512^3 volume (3 levels)."""
+    import torch
+    from paper_1002_2184_gb300 import api, build, synth
+    from paper_1002_2184_gb300 import autograd as ad
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.manual_seed(0)
+    rp = api.RaggedPlan(synth.ragged_shapes()[:64], dev, 0, 6)
+    xr = rp.empty()
+    xr.normal_()
+    cr, yr = rp.empty(), rp.empty()
+    rp.dwt(xr, cr)
+    rp.idwt(cr, yr)
+    del xr, cr, yr
+    gb = synth.GradBatch()
+    x = torch.randn(gb.shape, device=dev) * 0.3 + 0.5
+    pl = ad.DenoisePlan(x, gb.levels, gb.threshold, gb.l1_weight)
+    pl.forward()
+    pl.backward()
+    del x, pl
+    x = torch.randn(64, 1 << 20, device=dev)
+    c, y = torch.empty_like(x), torch.empty_like(x)
+    p1 = api.Plan(x, c, 8, y, one_d=True)
+    p1.dwt()
+    p1.idwt()
+    api.denoise1d(x, 8, 1.0, out=y)
+    api.swt1d(x, 1, out=torch.empty(64, 2, 1 << 20, device=dev))
+    api.filter_dwt1d(x, 8, api.DAUBECHIES4, out=c)
+    api.filter_idwt1d(c, 8, api.DAUBECHIES4, out=y)
+    del x, c, y
+    x = torch.randn(4, 4096, 4096, device=dev)
+    api.denoise2d(x, 5, 0.05, out=torch.empty_like(x))
+    del x
+    x = torch.randn(64, 2048, 2048, device=dev, dtype=torch.bfloat16)
+    c, y = torch.empty_like(x), torch.empty_like(x)
+    pb = api.Plan(x, c, 4, y)
+    pb.dwt()
+    pb.idwt()
+    del x, c, y
+    x = torch.randn(512, 512, 512, device=dev)
+    c, y = torch.empty_like(x), torch.empty_like(x)
+    api.dwt3d(x, 3, out=c)
+    api.idwt3d(c, 3, out=y)
+    torch.cuda.synchronize()
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -808,6 +863,9 @@ def run_reference(args):
 
 def main():
     args = parse_args()
+    if args.rows_once:
+        rows_once()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
