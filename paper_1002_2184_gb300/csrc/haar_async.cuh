@@ -33,18 +33,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // with a 16-byte aligned row the copy is made of aligned 16-byte pieces
 // (which may also bring a few neighbours, inside [0, P)); otherwise, e.g. for
 // windows that wrap around, each element is copied on its own.  Returns sh.
-template <typename T>
-__device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s, int cnt, int tid,
-                                     int nt) {
+// NT: the number of threads sharing the copy (a compile-time stride).
+template <int NT, typename T>
+__device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s, int cnt, int tid) {
   constexpr int V = fvec<T>();
-  const int sh = (int)(((s % V) + V) % V);
+  const int sh = (int)(s & (V - 1));  // s mod V, also for negative s (two's complement)
   const bool vec = ((uintptr_t)row % 16 == 0) && (P % V == 0) && s >= 0 && s + cnt <= P;
   if (vec) {
     const T* src = row + (s - sh);
     const int nv = (sh + cnt + V - 1) / V;
-    for (int i = tid; i < nv; i += nt) cp_async16(dst + i * V, src + i * V);
+    for (int i = tid; i < nv; i += NT) cp_async16(dst + i * V, src + i * V);
   } else {
-    for (int i = tid; i < cnt; i += nt) {
+    for (int i = tid; i < cnt; i += NT) {
       int64_t gpos = (s + i) % P;
       if (gpos < 0) gpos += P;
       cp_async_small<(int)sizeof(T)>(dst + sh + i, row + gpos);

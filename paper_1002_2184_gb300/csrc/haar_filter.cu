@@ -41,6 +41,7 @@ struct FilterArgs {
   int64_t chunks;
   double h[kFMaxTaps], g[kFMaxTaps];
   float hf[kFMaxTaps], gf[kFMaxTaps];  // the same, rounded once on the host
+  int woff[kFMaxLevels + 2];           // synthesis: offset of staged window w (a_L, d_L, ..., d_1)
 };
 
 template <typename T> struct FVec2;
@@ -78,14 +79,14 @@ __host__ __device__ constexpr int fidwt_stage_cap(int L) {
 // ---- analysis ----
 // One level: from the input A of this level (chunk + right halo r) the
 // low-pass outputs go to lo_dst, the details of the chunk to dl.
-template <typename T, int K>
+template <typename T, int K, int NT>
 __device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half, int m,
-                                          const T* h, const T* g, int tid, int nt) {
+                                          const T* h, const T* g, int tid) {
   using V2 = typename FVec2<T>::type;
   const V2* A2 = reinterpret_cast<const V2*>(A);
   if constexpr (K <= 4) {
     // two neighbouring outputs j, j + 1 per thread share K/2 + 1 pair loads
-    for (int p = tid; 2 * p < m; p += nt) {
+    for (int p = tid; 2 * p < m; p += NT) {
       T v[K + 2];
 #pragma unroll
       for (int t = 0; t <= K / 2; ++t) {
@@ -110,7 +111,7 @@ __device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half
   } else {
     // longer filters: one output per thread, neighbouring threads read
     // neighbouring pairs (no bank conflicts)
-    for (int j = tid; j < m; j += nt) {
+    for (int j = tid; j < m; j += NT) {
       T lo = T(0), hi = T(0);
 #pragma unroll
       for (int t = 0; t < K / 2; ++t) {
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
   // the chunk and the (K - 2)(2^L - 1) samples to its right that the coarser
   // levels' filters reach; k0 is a multiple of 16 bytes, so no shift
   int r = (K - 2) * ((1 << L) - 1);
-  stage(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x, blockDim.x);
+  stage<kFThreads>(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x);
   cp_async_wait_all();
   __syncthreads();
   int len = C, l = 1;
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
   for (; l <= L && (len >> 1) > 64; ++l) {
     const int rn = (r - (K - 2)) / 2;  // right halo of the next level
     const int half = len / 2;
-    dwt_level<T, K>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half, half + rn,
-                    h, g, threadIdx.x, blockDim.x);
+    dwt_level<T, K, kFThreads>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half,
+                               half + rn, h, g, threadIdx.x);
     __syncthreads();
     T* t = A;
     A = B;
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
     for (; l <= L; ++l) {
       const int rn = (r - (K - 2)) / 2;
       const int half = len / 2;
-      dwt_level<T, K>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half,
-                      half + rn, h, g, threadIdx.x, 32);
+      dwt_level<T, K, 32>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half,
+                          half + rn, h, g, threadIdx.x);
       __syncwarp();
       T* t = A;
       A = B;
@@ -190,11 +191,11 @@ __global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
 // One level l >= 2: pairs (2q, 2q+1) of level l-1, q = q0 + i, from a_l[q - t]
 // and d_l[q - t] (t < K/2), found at window index HL + i - t, written to B;
 // two pairs per thread share their loads.
-template <typename T, int K>
+template <typename T, int K, int NT>
 __device__ __forceinline__ void idwt_level(const T* Acur, const T* D, T* B, int np, int j00,
-                                           const T* h, const T* g, int tid, int nt) {
+                                           const T* h, const T* g, int tid) {
   constexpr int HL = K / 2 - 1;
-  for (int p = tid; 2 * p < np; p += nt) {
+  for (int p = tid; 2 * p < np; p += NT) {
     const int b1 = HL + 2 * p + 1;  // window index of the second pair
     T av[K / 2 + 1], dv[K / 2 + 1];
 #pragma unroll
@@ -233,15 +234,15 @@ template <> struct FVec16<double> { using type = double2; };
 // the 16-byte aligned buffers are compile-time constants: 0 for a_1 written
 // by level 2, (-HL) mod V for a staged window.  Eight values of each from
 // aligned 16-byte loads cover the HL + 4 that 4 pairs need.
-template <typename T, int K, bool A_STAGED>
+template <typename T, int K, bool A_STAGED, int NT>
 __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, bool v16_ok, int np,
-                                            const T* h, const T* g, int tid, int nt) {
+                                            const T* h, const T* g, int tid) {
   using VT = typename FVec16<T>::type;
   constexpr int V = fvec<T>();
   constexpr int HL = K / 2 - 1;
   constexpr int SD = (-HL) & (V - 1);  // shift of a staged level-1 window
   constexpr int SA = A_STAGED ? SD : 0;
-  for (int p = tid; 4 * p < np; p += nt) {
+  for (int p = tid; 4 * p < np; p += NT) {
     T ra[8], rd[8];
 #pragma unroll
     for (int i = 0; i < 8 / V; ++i) {
@@ -306,18 +307,14 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     for (int i = 0; i < l; ++i) e = (e + 1) / 2 + HL;
     return e;
   };
-  // stage the windows a_L, d_L, ..., d_1: window w by warp w mod 8 (each
-  // warp sets up only its own windows), then one wait for everything
+  // stage the windows a_L, d_L, ..., d_1: window w by warp w mod 8, at the
+  // offset the host computed, then one wait for everything
   {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    int off = 0;
-    for (int w = 0; w <= L; ++w) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int w = warp; w <= L; w += kFThreads / 32) {
       const int l = w == 0 ? L : L + 1 - w;
-      if (w % nwarps == warp) {
-        const int64_t nl = n >> l, s = (m0 >> l) - e_of(l);
-        stage(S + off, w == 0 ? c : c + nl, nl, s, (int)((end >> l) - s), lane, 32);
-      }
-      off += fidwt_seg_cap<T, K>(l);
+      const int64_t nl = n >> l, s = (m0 >> l) - e_of(l);
+      stage<32>(S + a.woff[w], w == 0 ? c : c + nl, nl, s, (int)((end >> l) - s), lane);
     }
   }
   __shared__ int s_e[kFMaxLevels + 1];
@@ -341,7 +338,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
         const T* D = S + doff2 + ((-s_e[l2]) & (V - 1));
         doff2 += fidwt_seg_cap<T, K>(l2);
         T* B = ((L - l2) & 1) ? P1 : P0;
-        idwt_level<T, K>(A2, D, B, (C >> l2) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x, 32);
+        idwt_level<T, K, 32>(A2, D, B, (C >> l2) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x);
         __syncwarp();
         A2 = B;
       }
@@ -359,18 +356,18 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     const T* D = S + doff + ((-s_e[l]) & (V - 1));
     doff += fidwt_seg_cap<T, K>(l);
     T* B = ((L - l) & 1) ? P1 : P0;
-    idwt_level<T, K>(Acur, D, B, (C >> l) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x,
-                     blockDim.x);
+    idwt_level<T, K, kFThreads>(Acur, D, B, (C >> l) + (em + 1) / 2, -(em & 1), h, g,
+                                threadIdx.x);
     __syncthreads();
     Acur = B;
   }
   // level 1: C/2 pairs, straight to the output (doff is the d_1 window)
   const bool v16_ok = (uintptr_t)(x + m0) % 16 == 0;
   if (L == 1)
-    idwt_level1<T, K, true>(S, S + doff, x + m0, v16_ok, C >> 1, h, g, threadIdx.x, blockDim.x);
+    idwt_level1<T, K, true, kFThreads>(S, S + doff, x + m0, v16_ok, C >> 1, h, g, threadIdx.x);
   else
-    idwt_level1<T, K, false>(Acur, S + doff, x + m0, v16_ok, C >> 1, h, g, threadIdx.x,
-                             blockDim.x);
+    idwt_level1<T, K, false, kFThreads>(Acur, S + doff, x + m0, v16_ok, C >> 1, h, g,
+                                        threadIdx.x);
 }
 
 template <typename T, int K>
@@ -397,6 +394,27 @@ cudaError_t filter_launch_k(bool fwd, const FilterArgs& a, int64_t total, cudaSt
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// Offsets of the synthesis windows a_L, d_L, ..., d_1 in the staging area.
+template <typename T, int K>
+void window_offsets_k(FilterArgs& a) {
+  int off = 0;
+  for (int w = 0; w <= a.levels; ++w) {
+    const int l = w == 0 ? a.levels : a.levels + 1 - w;
+    a.woff[w] = off;
+    off += fidwt_seg_cap<T, K>(l);
+  }
+}
+template <typename T>
+cudaError_t window_offsets(FilterArgs& a, int K) {
+  switch (K) {
+    case 2: window_offsets_k<T, 2>(a); return cudaSuccess;
+    case 4: window_offsets_k<T, 4>(a); return cudaSuccess;
+    case 6: window_offsets_k<T, 6>(a); return cudaSuccess;
+    case 8: window_offsets_k<T, 8>(a); return cudaSuccess;
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -444,6 +462,9 @@ int filter_entry(const void* in, void* out, int dtype, int64_t rows, int64_t n, 
     a.hf[k] = (float)a.h[k];
     a.gf[k] = (float)a.g[k];
   }
+  const cudaError_t e0 = dtype == HAAR_F64 ? window_offsets<double>(a, ntaps)
+                                           : window_offsets<float>(a, ntaps);
+  if (e0 != cudaSuccess) return HAAR_EINVAL;
   const cudaError_t e = dtype == HAAR_F64 ? filter_launch<double>(fwd, a, ntaps, (cudaStream_t)stream)
                                           : filter_launch<float>(fwd, a, ntaps, (cudaStream_t)stream);
   if (e != cudaSuccess) {

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_swt(const SwtArgs a) {
   const int H = (1 << a.levels) - 1;
   const T* x = static_cast<const T*>(a.in) + row * n;
   T* out = static_cast<T*>(a.out) + row * (a.levels + 1) * n;
-  stage(A, x, n, k0, C + H, threadIdx.x, blockDim.x);  // k0 is 16-byte aligned: no shift
+  stage<256>(A, x, n, k0, C + H, threadIdx.x);  // k0 is 16-byte aligned: no shift
   cp_async_wait_all();
   __syncthreads();
   const T r = Consts<T>::s();
@@ -92,13 +92,12 @@ __global__ void __launch_bounds__(256) k_iswt(const SwtArgs a) {
   T* x = static_cast<T*>(a.out) + row * n;
   const int L = a.levels;
   int H = (1 << L) - 1;  // left halo of a_L
-  const T* A = bufA + stage(bufA, c, n, k0 - H, C + H, threadIdx.x, blockDim.x);
+  const T* A = bufA + stage<256>(bufA, c, n, k0 - H, C + H, threadIdx.x);
   T* B = bufB;
   const T q = Consts<T>::s() * T(0.5);
   for (int l = L; l >= 1; --l) {
     const int s = 1 << (l - 1);
-    const T* D = bufD + stage(bufD, c + (int64_t)l * n, n, k0 - H, C + H, threadIdx.x,
-                              blockDim.x);
+    const T* D = bufD + stage<256>(bufD, c + (int64_t)l * n, n, k0 - H, C + H, threadIdx.x);
     cp_async_wait_all();
     __syncthreads();
     const int Hn = H - s;  // left halo of a_{l-1}
