@@ -377,8 +377,16 @@ __device__ __forceinline__ Img2 pass_image(const Pass& p, int64_t b, bool analys
 // Strided-batch kernels.  Analysis block of warps: 1 x 8 (32 x 256 px) for
 // L <= 5, 2 x 4 (64 x 128 px) for L = 6.  Synthesis: 1 x 8 for every L.
 // ---------------------------------------------------------------------------
+// Analysis: inputs of at most 2 bytes carry half the bytes per instruction
+// or less, so more resident warps hide more latency: registers capped for 6
+// blocks per SM (bf16 64 x 2048^2, 4 levels: 0.167 against 0.191 ms).  For
+// fp32 the cap measured slower, so none.
+template <typename Tin>
+constexpr int dwt_min_blocks() {
+  return sizeof(Tin) <= 2 ? 6 : 1;
+}
 template <typename Tin, typename Tout, int L>
-__global__ void __launch_bounds__(256) k_dwt2d_fast(const Pass p) {
+__global__ void __launch_bounds__(256, dwt_min_blocks<Tin>()) k_dwt2d_fast(const Pass p) {
   pdl_wait();
   pdl_trigger();
   using A = typename AccT<Tin>::type;
