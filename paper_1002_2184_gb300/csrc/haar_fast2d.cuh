@@ -379,11 +379,12 @@ __device__ __forceinline__ Img2 pass_image(const Pass& p, int64_t b, bool analys
 // ---------------------------------------------------------------------------
 // Analysis: inputs of at most 2 bytes carry half the bytes per instruction
 // or less, so more resident warps hide more latency: registers capped for 6
-// blocks per SM (bf16 64 x 2048^2, 4 levels: 0.167 against 0.191 ms).  For
-// fp32 the cap measured slower, so none.
+// blocks per SM (bf16 64 x 2048^2, 4 levels: 0.167 against 0.191 ms).  fp32
+// keeps its 5 blocks (42 registers; a cap for 6 measured slower); fp64, the
+// verification path, is not capped.
 template <typename Tin>
 constexpr int dwt_min_blocks() {
-  return sizeof(Tin) <= 2 ? 6 : 1;
+  return sizeof(Tin) <= 2 ? 6 : sizeof(Tin) == 4 ? 5 : 1;
 }
 template <typename Tin, typename Tout, int L>
 __global__ void __launch_bounds__(256, dwt_min_blocks<Tin>()) k_dwt2d_fast(const Pass p) {
