@@ -130,12 +130,18 @@ __device__ __forceinline__ void load8(const __half* p, float v[8]) {
     v[2 * k + 1] = f.y;
   }
 }
+// Byte k of w as a float, exactly: one byte permute builds the bit pattern
+// of 2^23 + byte (the byte lands in the low mantissa bits under the exponent
+// of 2^23), one subtraction removes 2^23.
+__device__ __forceinline__ float u8_to_f32(uint32_t w, int k) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + (unsigned)k)) - 8388608.0f;
+}
 __device__ __forceinline__ void load8(const uint8_t* p, float v[8]) {
   uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    v[k] = (float)((u.x >> (8 * k)) & 0xffu);
-    v[4 + k] = (float)((u.y >> (8 * k)) & 0xffu);
+    v[k] = u8_to_f32(u.x, k);
+    v[4 + k] = u8_to_f32(u.y, k);
   }
 }
 
