@@ -287,8 +287,12 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.levels;
   T* S = reinterpret_cast<T*>(smem_raw);
-  T* P0 = S + fidwt_stage_cap<T, K>(L);
-  T* P1 = P0 + fidwt_seg_cap<T, K>(1);
+  // a_{l-1}, written by level l, goes to P[(l - 1) & 1]: a_1, a_3, ... to P1
+  // (sized for a_1), a_2, a_4, ... to P0 (sized for a_2); a level reads one and
+  // writes the other.  Smaller than two a_1-sized buffers: 7 blocks/SM for
+  // fp32 instead of 6 (Daubechies-4, 8 levels: 5 % faster).
+  T* P1 = S + fidwt_stage_cap<T, K>(L);
+  T* P0 = P1 + fidwt_seg_cap<T, K>(1);
   T h[K], g[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
         const int em = s_e[l2 - 1];
         const T* D = S + doff2 + ((-s_e[l2]) & (V - 1));
         doff2 += fidwt_seg_cap<T, K>(l2);
-        T* B = ((L - l2) & 1) ? P1 : P0;
+        T* B = ((l2 - 1) & 1) ? P1 : P0;
         idwt_level<T, K, 32>(A2, D, B, (C >> l2) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x);
         __syncwarp();
         A2 = B;
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     // every thread advances to the first fine level
     for (; l >= 2 && (C >> l) <= 64; --l) {
       doff += fidwt_seg_cap<T, K>(l);
-      Acur = ((L - l) & 1) ? P1 : P0;
+      Acur = ((l - 1) & 1) ? P1 : P0;
     }
     __syncthreads();
   }
@@ -355,7 +359,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     const int em = s_e[l - 1];
     const T* D = S + doff + ((-s_e[l]) & (V - 1));
     doff += fidwt_seg_cap<T, K>(l);
-    T* B = ((L - l) & 1) ? P1 : P0;
+    T* B = ((l - 1) & 1) ? P1 : P0;
     idwt_level<T, K, kFThreads>(Acur, D, B, (C >> l) + (em + 1) / 2, -(em & 1), h, g,
                                 threadIdx.x);
     __syncthreads();
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
 template <typename T, int K>
 size_t filter_smem(bool fwd, int L) {
   const int elems = fwd ? fdwt_cap_a<T, K>(L) + fdwt_cap_b<T, K>(L)
-                        : fidwt_stage_cap<T, K>(L) + 2 * fidwt_seg_cap<T, K>(1);
+                        : fidwt_stage_cap<T, K>(L) + fidwt_seg_cap<T, K>(1) + fidwt_seg_cap<T, K>(2);
   return (size_t)elems * sizeof(T);
 }
 
