@@ -15,7 +15,10 @@
 // Work is cut into chunks of 4096 level-0 positions (4096 / 2^l coefficients
 // at level l).  Analysis: the chunk plus a right halo of (K - 2)(2^L - 1)
 // samples (wrapped) is staged in shared memory with asynchronous 16-byte
-// copies and every level is fused there.  Synthesis: a_L and the window of
+// copies and every level is fused there, two levels per pass: a thread takes
+// 8 consecutive inputs of level l, makes 4 outputs of level l + 1 (and the
+// K - 2 low-pass ones after them) in registers and from those 2 outputs of
+// level l + 2, so level l + 1 never touches shared memory.  Synthesis: a_L and the window of
 // every d_l the chunk needs (K/2 - 1 extra coefficients per level on the
 // left) are staged in one go, the levels run coarsest first and level 1 is
 // written straight to the output.
@@ -31,7 +34,8 @@ namespace fh {
 constexpr int kFChunk = 4096;  // level-0 positions per block
 constexpr int kFMaxLevels = 10;
 constexpr int kFMaxTaps = 8;
-constexpr int kFThreads = 256;
+constexpr int kFThreads = 128;   // synthesis block
+constexpr int kFThreadsA = 128;  // analysis block
 
 struct FilterArgs {
   const void* in;
@@ -47,20 +51,25 @@ struct FilterArgs {
 template <typename T> struct FVec2;
 template <> struct FVec2<float> { using type = float2; };
 template <> struct FVec2<double> { using type = double2; };
+template <typename T> struct FVec16;
+template <> struct FVec16<float> { using type = float4; };
+template <> struct FVec16<double> { using type = double2; };
 
 
 __host__ __device__ constexpr int fround(int v, int m) { return (v + m - 1) / m * m; }
 
 
 // ---- shared-memory footprints (host and device agree on these) ----
-// analysis: staged window (chunk + right halo) and one half-size buffer
+// analysis: staged window (chunk + right halo) and one quarter-size buffer
+// for a_2, a_6, ... (a_4, a_8, ... go back to the first); both with 2 * 16
+// bytes of slack for the reads past the end
 template <typename T, int K>
 __host__ __device__ constexpr int fdwt_cap_a(int L) {
   return fround(kFChunk + (K - 2) * ((1 << L) - 1) + 2 * fvec<T>(), fvec<T>());
 }
 template <typename T, int K>
 __host__ __device__ constexpr int fdwt_cap_b(int L) {
-  return fround(kFChunk / 2 + (K - 2) * ((1 << L) - 1) / 2 + fvec<T>(), fvec<T>());
+  return fround(kFChunk / 4 + (K - 2) * ((1 << L) - 1) / 4 + 2 * fvec<T>(), fvec<T>());
 }
 // synthesis: the window of level l (a_l or d_l) spans (chunk >> l) + at most
 // 2 (K/2 - 1) + 1 positions; every window is staged with a 16-byte slack and
@@ -127,8 +136,108 @@ __device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half
   }
 }
 
+// Two levels in one pass.  X holds this level's input: len samples of the
+// chunk and a right halo r; m2 = len/4 + r2 outputs of level l + 2 are made
+// (r2 = (r - 3(K - 2)) / 4, the halo the levels after it need).  Unit u reads
+// X[8u, 8u + 3K + 2): a_{l+1}[4u + j] for j < K + 2 (the last K - 2 belong to
+// the next unit as well and are made twice), d_{l+1}[4u + j] for j < 4, then
+// a_{l+2} and d_{l+2} at 2u and 2u + 1.  Outputs past the ends (m2, len/2,
+// len/4) are computed from the buffer's slack and not stored: the last unit
+// reads up to X[len + r + 5] (fp32) or X[len + r + 3] (fp64), inside the
+// 2 * 16 bytes of slack every staging buffer has.
 template <typename T, int K>
-__global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
+__device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T* g, T (&e1)[4],
+                                          T (&a2)[2], T (&e2)[2]) {
+  using VT = typename FVec16<T>::type;
+  constexpr int V = fvec<T>();
+  constexpr int NW = (3 * K + 2 + V - 1) / V;  // 16-byte loads per unit
+  T x[NW * V];
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    *reinterpret_cast<VT*>(x + i * V) = reinterpret_cast<const VT*>(X + 8 * u)[i];
+  T a1[K + 2];
+#pragma unroll
+  for (int j = 0; j < K + 2; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) s = fma(h[k], x[2 * j + k], s);
+    a1[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) s = fma(g[k], x[2 * j + k], s);
+    e1[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    T s = T(0), d = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      s = fma(h[k], a1[2 * j + k], s);
+      d = fma(g[k], a1[2 * j + k], d);
+    }
+    a2[j] = s;
+    e2[j] = d;
+  }
+}
+
+// Units u < len/8 have all their outputs inside: with VEC (every output
+// vector aligned) they store without a guard.  The rest -- the halo units,
+// whose only stored outputs are a_{l+2}, and the last unit of a ragged
+// chunk -- store one by one under guards.
+template <typename T, int K, int NT, bool VEC>
+__device__ __forceinline__ void dwt_pair(const T* X, T* lo, T* d1, T* d2, int len, int m2,
+                                         const T* h, const T* g, int tid) {
+  using V2 = typename FVec2<T>::type;
+  const int nfull = VEC ? len >> 3 : 0;
+  for (int u = tid; u < nfull; u += NT) {
+    T e1[4], a2[2], e2[2];
+    pair_unit<T, K>(X, u, h, g, e1, a2, e2);
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(d1 + 4 * u) = make_float4(e1[0], e1[1], e1[2], e1[3]);
+    } else {
+      *reinterpret_cast<V2*>(d1 + 4 * u) = V2{e1[0], e1[1]};
+      *reinterpret_cast<V2*>(d1 + 4 * u + 2) = V2{e1[2], e1[3]};
+    }
+    *reinterpret_cast<V2*>(d2 + 2 * u) = V2{e2[0], e2[1]};
+    *reinterpret_cast<V2*>(lo + 2 * u) = V2{a2[0], a2[1]};
+  }
+  const int n1 = len >> 1, n2 = len >> 2;
+  for (int u = nfull + tid; 2 * u < m2; u += NT) {
+    T e1[4], a2[2], e2[2];
+    pair_unit<T, K>(X, u, h, g, e1, a2, e2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (4 * u + i < n1) d1[4 * u + i] = e1[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (2 * u + i < n2) d2[2 * u + i] = e2[i];
+      if (2 * u + i < m2) lo[2 * u + i] = a2[i];
+    }
+  }
+}
+
+// One step on NT threads: the low-pass outputs go to shared memory (Y) or,
+// on the last level, to the output; VEC when every output vector of a full
+// unit is aligned.
+template <typename T, int K, int NT>
+__device__ __forceinline__ void dwt_pair_step(const T* X, T* Y, T* out, T* d1, T* d2, bool last,
+                                              int len, int m2, const T* h, const T* g, int tid) {
+  const bool vec = (uintptr_t)d1 % 16 == 0 && (uintptr_t)d2 % (2 * sizeof(T)) == 0 &&
+                   (uintptr_t)out % (2 * sizeof(T)) == 0;
+  if (!last) {
+    if (vec) dwt_pair<T, K, NT, true>(X, Y, d1, d2, len, m2, h, g, tid);
+    else dwt_pair<T, K, NT, false>(X, Y, d1, d2, len, m2, h, g, tid);
+  } else {
+    if (vec) dwt_pair<T, K, NT, true>(X, out, d1, d2, len, m2, h, g, tid);
+    else dwt_pair<T, K, NT, false>(X, out, d1, d2, len, m2, h, g, tid);
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kFThreadsA) k_filter_dwt(const FilterArgs a) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -149,36 +258,46 @@ __global__ void __launch_bounds__(kFThreads) k_filter_dwt(const FilterArgs a) {
   // the chunk and the (K - 2)(2^L - 1) samples to its right that the coarser
   // levels' filters reach; k0 is a multiple of 16 bytes, so no shift
   int r = (K - 2) * ((1 << L) - 1);
-  stage<kFThreads>(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x);
+  stage<kFThreadsA>(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x);
   cp_async_wait_all();
   __syncthreads();
-  int len = C, l = 1;
-  // fine levels: the whole block
-  for (; l <= L && (len >> 1) > 64; ++l) {
-    const int rn = (r - (K - 2)) / 2;  // right halo of the next level
-    const int half = len / 2;
-    dwt_level<T, K, kFThreads>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half,
-                               half + rn, h, g, threadIdx.x);
-    __syncthreads();
-    T* t = A;
-    A = B;
-    B = t;
-    len = half;
-    r = rn;
-  }
-  // coarse levels (at most 64 low-pass outputs of the chunk): warp 0 alone
-  if (l <= L && threadIdx.x < 32) {
-    for (; l <= L; ++l) {
-      const int rn = (r - (K - 2)) / 2;
-      const int half = len / 2;
-      dwt_level<T, K, 32>(A, l == L ? out + (k0 >> L) : B, out + (n >> l) + (k0 >> l), half,
-                          half + rn, h, g, threadIdx.x);
+  T* X = A;
+  T* Y = B;
+  int len = C, l = 0;  // l levels done; X holds a_l (len of the chunk, halo r)
+  bool solo = false;   // warp 0 alone from here on
+  // pairs of levels
+  for (; L - l >= 2; l += 2) {
+    const int r2 = (r - 3 * (K - 2)) / 4;
+    const int m2 = len / 4 + r2;
+    T* d1 = out + (n >> (l + 1)) + (k0 >> (l + 1));
+    T* d2 = out + (n >> (l + 2)) + (k0 >> (l + 2));
+    T* lo = out + (k0 >> L);
+    const bool last = l + 2 == L;
+    if (!solo && (m2 + 1) / 2 > 64) {
+      dwt_pair_step<T, K, kFThreadsA>(X, Y, lo, d1, d2, last, len, m2, h, g, threadIdx.x);
+      __syncthreads();
+    } else {
+      // at most 64 units: warp 0 alone, the other warps are done
+      if (threadIdx.x >= 32) return;
+      solo = true;
+      dwt_pair_step<T, K, 32>(X, Y, lo, d1, d2, last, len, m2, h, g, threadIdx.x);
       __syncwarp();
-      T* t = A;
-      A = B;
-      B = t;
-      len = half;
-      r = rn;
+    }
+    T* t = X;
+    X = Y;
+    Y = t;
+    len /= 4;
+    r = r2;
+  }
+  // an odd number of levels: the coarsest one alone
+  if (l < L) {
+    const int half = len / 2;
+    T* lo = out + (k0 >> L);
+    T* dl = out + (n >> L) + (k0 >> L);
+    if (!solo && half > 64) {
+      dwt_level<T, K, kFThreadsA>(X, lo, dl, half, half, h, g, threadIdx.x);
+    } else if (threadIdx.x < 32) {
+      dwt_level<T, K, 32>(X, lo, dl, half, half, h, g, threadIdx.x);
     }
   }
 }
@@ -224,10 +343,6 @@ __device__ __forceinline__ void idwt_level(const T* Acur, const T* D, T* B, int 
     }
   }
 }
-
-template <typename T> struct FVec16;
-template <> struct FVec16<float> { using type = float4; };
-template <> struct FVec16<double> { using type = double2; };
 
 // Level 1, the largest: a thread makes 4 pairs (8 output samples).  The
 // window start of both a_1 and d_1 is lo(1) = m0/2 - HL, so their shifts in
@@ -389,7 +504,7 @@ cudaError_t filter_launch_k(bool fwd, const FilterArgs& a, int64_t total, cudaSt
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)total);
-  cfg.blockDim = dim3(kFThreads);
+  cfg.blockDim = dim3(fwd ? kFThreadsA : kFThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
