@@ -84,6 +84,25 @@ __host__ __device__ constexpr int fidwt_stage_cap(int L) {
   for (int l = 1; l <= L; ++l) t += fidwt_seg_cap<T, K>(l);
   return t;
 }
+// synthesis intermediates: a_2, a_6, a_10 in the big buffer, a_4, a_8 in the
+// small one (a pass reads one and writes the other); each holds its window,
+// the 8 values a unit writes past it and the reads past it
+template <typename T, int K>
+__host__ __device__ constexpr int fidwt_big_cap() {
+  return fround((kFChunk >> 2) + 4 * (K / 2 - 1) + 16 + 2 * fvec<T>(), fvec<T>());
+}
+template <typename T, int K>
+__host__ __device__ constexpr int fidwt_small_cap() {
+  return fround((kFChunk >> 4) + 4 * (K / 2 - 1) + 16 + 2 * fvec<T>(), fvec<T>());
+}
+// e_l of the synthesis window start lo(l) = (m0 >> l) - e_l: e_0 = 0,
+// e_l = ceil(e_{l-1} / 2) + K/2 - 1 (the same for every chunk)
+template <int K>
+__host__ __device__ constexpr int fe(int l) {
+  int e = 0;
+  for (int i = 0; i < l; ++i) e = (e + 1) / 2 + K / 2 - 1;
+  return e;
+}
 
 // ---- analysis ----
 // One level: from the input A of this level (chunk + right halo r) the
@@ -303,15 +322,17 @@ __global__ void __launch_bounds__(kFThreadsA) k_filter_dwt(const FilterArgs a) {
 }
 
 // ---- synthesis ----
-// window of level l: [lo(l), (m0 + C) >> l) with lo(l) = floor(lo(l-1) / 2) - HL,
-// lo(0) = m0.  As m0 is a multiple of 2^12, lo(l) = (m0 >> l) - e_l with
-// e_0 = 0, e_l = ceil(e_{l-1} / 2) + HL, the same for every chunk.
+// Window of level l: positions [lo(l), (m0 + C) >> l), lo(l) = (m0 >> l) - e_l.
+// A "window-origin" pointer W has W[k] = the value at lo(l) + k.  Pairs of
+// level l - 1 are q = lo(l) + HL + i; pair i reads a_l and d_l at window
+// indices i + HL - t (t < K/2) and writes a_{l-1} at window indices
+// 2i + p - (e_{l-1} mod 2).
 //
-// One level l >= 2: pairs (2q, 2q+1) of level l-1, q = q0 + i, from a_l[q - t]
-// and d_l[q - t] (t < K/2), found at window index HL + i - t, written to B;
-// two pairs per thread share their loads.
+// One level: pairs (2q, 2q+1) of level l-1, q = q0 + i, written to B[4p ..]
+// (B index = window index + (e_{l-1} mod 2)); two pairs per thread share
+// their loads.
 template <typename T, int K, int NT>
-__device__ __forceinline__ void idwt_level(const T* Acur, const T* D, T* B, int np, int j00,
+__device__ __forceinline__ void idwt_level(const T* Acur, const T* D, T* B, int np,
                                            const T* h, const T* g, int tid) {
   constexpr int HL = K / 2 - 1;
   for (int p = tid; 2 * p < np; p += NT) {
@@ -334,29 +355,166 @@ __device__ __forceinline__ void idwt_level(const T* Acur, const T* D, T* B, int 
       o0 = fma(h[2 * t + 1], av[t + 1], o0);
       o0 = fma(g[2 * t + 1], dv[t + 1], o0);
     }
-    const int j = j00 + 4 * p;
-    if (j >= 0) B[j] = e0;
-    B[j + 1] = o0;
+    T* b = B + 4 * p;
+    b[0] = e0;
+    b[1] = o0;
     if (2 * p + 1 < np) {
-      B[j + 2] = e1;
-      B[j + 3] = o1;
+      b[2] = e1;
+      b[3] = o1;
     }
   }
 }
 
-// Level 1, the largest: a thread makes 4 pairs (8 output samples).  The
-// window start of both a_1 and d_1 is lo(1) = m0/2 - HL, so their shifts in
-// the 16-byte aligned buffers are compile-time constants: 0 for a_1 written
-// by level 2, (-HL) mod V for a staged window.  Eight values of each from
-// aligned 16-byte loads cover the HL + 4 that 4 pairs need.
-template <typename T, int K, bool A_STAGED, int NT>
+// Two levels in one pass (l and l - 1): a unit makes pairs i' = 4u .. 4u + 3
+// of level l - 1, i.e. 8 values of a_{l-2}.  They read a_{l-1} at window
+// indices 4u .. 4u + 3 + HL, which come from the NP pairs of level l that
+// start at 2u (made in registers; with ODD = e_{l-1} mod 2 the window index
+// 4u + j is value j + ODD of those pairs), and those read a_l, d_l at window
+// indices 2u .. 2u + NP - 1 + HL.  av, dv: a_l, d_l from 2u; d1: d_{l-1}
+// from 4u.  y[2k + p] is output p of pair 4u + k.
+template <int K, bool ODD>
+struct SynShape {
+  static constexpr int HL = K / 2 - 1;
+  static constexpr int NP = (5 + HL + (ODD ? 1 : 0)) / 2;
+  static constexpr int NA = NP + HL;
+};
+
+template <typename T, int K, bool ODD>
+__device__ __forceinline__ void syn_unit(const T (&av)[SynShape<K, ODD>::NA],
+                                         const T (&dv)[SynShape<K, ODD>::NA], const T (&d1)[K / 2 + 3],
+                                         const T* h, const T* g, T (&y)[8]) {
+  using S = SynShape<K, ODD>;
+  constexpr int HL = S::HL;
+  T z[2 * S::NP];
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) {
+    T e = T(0), o = T(0);
+#pragma unroll
+    for (int t = 0; t < K / 2; ++t) {
+      e = fma(h[2 * t], av[i + HL - t], e);
+      e = fma(g[2 * t], dv[i + HL - t], e);
+      o = fma(h[2 * t + 1], av[i + HL - t], o);
+      o = fma(g[2 * t + 1], dv[i + HL - t], o);
+    }
+    z[2 * i] = e;
+    z[2 * i + 1] = o;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T e = T(0), o = T(0);
+#pragma unroll
+    for (int t = 0; t < K / 2; ++t) {
+      const T a = z[k + HL - t + (ODD ? 1 : 0)], d = d1[k + HL - t];
+      e = fma(h[2 * t], a, e);
+      e = fma(g[2 * t], d, e);
+      o = fma(h[2 * t + 1], a, o);
+      o = fma(g[2 * t + 1], d, o);
+    }
+    y[2 * k] = e;
+    y[2 * k + 1] = o;
+  }
+}
+
+// A coarse pass (levels l, l - 1 with l - 2 >= 2): window-origin pointers,
+// element loads, 8 values per unit to P[8u ..] (P index = window index +
+// (e_{l-2} mod 2), 16-byte aligned).
+template <typename T, int K, int NT, bool ODD>
+__device__ __forceinline__ void idwt_pair(const T* Aw, const T* Dw, const T* Dw1, T* P, int units,
+                                          const T* h, const T* g, int tid) {
+  using S = SynShape<K, ODD>;
+  using VT = typename FVec16<T>::type;
+  constexpr int V = fvec<T>();
+  for (int u = tid; u < units; u += NT) {
+    T av[S::NA], dv[S::NA], d1[K / 2 + 3];
+#pragma unroll
+    for (int s = 0; s < S::NA; ++s) {
+      av[s] = Aw[2 * u + s];
+      dv[s] = Dw[2 * u + s];
+    }
+#pragma unroll
+    for (int j = 0; j < K / 2 + 3; ++j) d1[j] = Dw1[4 * u + j];
+    T y[8];
+    syn_unit<T, K, ODD>(av, dv, d1, h, g, y);
+#pragma unroll
+    for (int i = 0; i < 8 / V; ++i) {
+      VT w;
+      if constexpr (sizeof(T) == 4) w = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+      else w = VT{y[2 * i], y[2 * i + 1]};
+      reinterpret_cast<VT*>(P + 8 * u)[i] = w;
+    }
+  }
+}
+
+// The last pass (levels 2 and 1), straight to the output.  Every window
+// shift is a compile-time constant here (e_1 and e_2 depend on K only), so
+// a_2 and d_2 come in 2-element and d_1 in 16-byte aligned vectors from the
+// buffer starts Ab, D2b, D1b.  a_2 sits in the big buffer (shift e_2 mod 2)
+// or, for two levels, in its staged window.
+template <typename T, int K, int NT, bool A_STAGED>
+__device__ __forceinline__ void idwt_pair_last(const T* Ab, const T* D2b, const T* D1b, T* xo,
+                                               bool v_ok, int np1, const T* h, const T* g,
+                                               int tid) {
+  using V2 = typename FVec2<T>::type;
+  using VT = typename FVec16<T>::type;
+  constexpr int V = fvec<T>();
+  constexpr int e1 = fe<K>(1), e2 = fe<K>(2);
+  constexpr bool ODD = e1 & 1;
+  using S = SynShape<K, ODD>;
+  constexpr int SA = A_STAGED ? ((-e2) & (V - 1)) : (e2 & 1);
+  constexpr int SD2 = (-e2) & (V - 1);
+  constexpr int SD1 = (-e1) & (V - 1);
+  constexpr int NLA = (SA + S::NA + 1) / 2, NLD = (SD2 + S::NA + 1) / 2;
+  static_assert(SD1 + K / 2 + 3 <= 8, "d_1 reads stay inside the 8 loaded values");
+  for (int u = tid; 4 * u < np1; u += NT) {
+    T ra[2 * NLA], rd[2 * NLD], r1[8];
+#pragma unroll
+    for (int i = 0; i < NLA; ++i) {
+      const V2 w = reinterpret_cast<const V2*>(Ab + 2 * u)[i];
+      ra[2 * i] = w.x;
+      ra[2 * i + 1] = w.y;
+    }
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const V2 w = reinterpret_cast<const V2*>(D2b + 2 * u)[i];
+      rd[2 * i] = w.x;
+      rd[2 * i + 1] = w.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 8 / V; ++i)
+      *reinterpret_cast<VT*>(r1 + i * V) = reinterpret_cast<const VT*>(D1b + 4 * u)[i];
+    T av[S::NA], dv[S::NA], d1[K / 2 + 3];
+#pragma unroll
+    for (int s = 0; s < S::NA; ++s) {
+      av[s] = ra[s + SA];
+      dv[s] = rd[s + SD2];
+    }
+#pragma unroll
+    for (int j = 0; j < K / 2 + 3; ++j) d1[j] = r1[j + SD1];
+    T y[8];
+    syn_unit<T, K, ODD>(av, dv, d1, h, g, y);
+    T* xp = xo + 8 * u;
+    if (v_ok && 4 * u + 3 < np1) {
+      store8(xp, y);  // whole sectors where the address allows
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (4 * u + k < np1) {
+          xp[2 * k] = y[2 * k];
+          xp[2 * k + 1] = y[2 * k + 1];
+        }
+    }
+  }
+}
+
+// One level alone (a single-level transform): a thread makes 4 pairs from
+// the staged a_1 and d_1 windows (shift (-HL) mod V for both).
+template <typename T, int K, int NT>
 __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, bool v16_ok, int np,
                                             const T* h, const T* g, int tid) {
   using VT = typename FVec16<T>::type;
   constexpr int V = fvec<T>();
   constexpr int HL = K / 2 - 1;
-  constexpr int SD = (-HL) & (V - 1);  // shift of a staged level-1 window
-  constexpr int SA = A_STAGED ? SD : 0;
+  constexpr int SD = (-HL) & (V - 1);
   for (int p = tid; 4 * p < np; p += NT) {
     T ra[8], rd[8];
 #pragma unroll
@@ -370,7 +528,7 @@ __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, boo
       T e = T(0), o = T(0);
 #pragma unroll
       for (int t = 0; t < K / 2; ++t) {
-        const T av = ra[HL + k - t + SA], dv = rd[HL + k - t + SD];
+        const T av = ra[HL + k - t + SD], dv = rd[HL + k - t + SD];
         e = fma(h[2 * t], av, e);
         e = fma(g[2 * t], dv, e);
         o = fma(h[2 * t + 1], av, o);
@@ -381,7 +539,7 @@ __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, boo
     }
     T* xp = xo + 8 * p;
     if (v16_ok && 4 * p + 3 < np) {
-      store8(xp, y);  // whole sectors where the address allows
+      store8(xp, y);
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -398,16 +556,12 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   pdl_wait();
   pdl_trigger();
   constexpr int V = fvec<T>();
-  constexpr int HL = K / 2 - 1;  // extra coefficients needed on the left
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.levels;
   T* S = reinterpret_cast<T*>(smem_raw);
-  // a_{l-1}, written by level l, goes to P[(l - 1) & 1]: a_1, a_3, ... to P1
-  // (sized for a_1), a_2, a_4, ... to P0 (sized for a_2); a level reads one and
-  // writes the other.  Smaller than two a_1-sized buffers: 7 blocks/SM for
-  // fp32 instead of 6 (Daubechies-4, 8 levels: 5 % faster).
-  T* P1 = S + fidwt_stage_cap<T, K>(L);
-  T* P0 = P1 + fidwt_seg_cap<T, K>(1);
+  T* Pbig = S + fidwt_stage_cap<T, K>(L);
+  T* Psmall = Pbig + fidwt_big_cap<T, K>();
+  auto P = [&](int l) { return ((l >> 1) & 1) ? Pbig : Psmall; };  // holds a_l, l even
   T h[K], g[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -421,78 +575,91 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   const int64_t end = m0 + C;
   const T* c = static_cast<const T*>(a.in) + row * n;
   T* x = static_cast<T*>(a.out) + row * n;
-  auto e_of = [](int l) {  // e_l of the window start lo(l) = (m0 >> l) - e_l
-    int e = 0;
-    for (int i = 0; i < l; ++i) e = (e + 1) / 2 + HL;
-    return e;
-  };
-  // stage the windows a_L, d_L, ..., d_1: window w by warp w mod 8, at the
+  // stage the windows a_L, d_L, ..., d_1: window w by warp w mod 4, at the
   // offset the host computed, then one wait for everything
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int w = warp; w <= L; w += kFThreads / 32) {
       const int l = w == 0 ? L : L + 1 - w;
-      const int64_t nl = n >> l, s = (m0 >> l) - e_of(l);
+      const int64_t nl = n >> l, s = (m0 >> l) - fe<K>(l);
       stage<32>(S + a.woff[w], w == 0 ? c : c + nl, nl, s, (int)((end >> l) - s), lane);
     }
   }
-  __shared__ int s_e[kFMaxLevels + 1];
-  if (threadIdx.x <= (unsigned)L) s_e[threadIdx.x] = e_of(threadIdx.x);
   cp_async_wait_all();
   __syncthreads();
-  // With m0 a multiple of 2^12, everything a level needs is a small integer:
-  //   shift of the window in its buffer  (-e_l) mod V    ((m0 >> l) = 0 mod V)
-  //   pairs of level l-1                 np  = (C >> l) + ceil(e_{l-1} / 2)
-  //   first output in the window         j00 = -(e_{l-1} mod 2)
-  const T* Acur = S + ((-s_e[L]) & (V - 1));
-  int doff = fidwt_seg_cap<T, K>(L);
+  const bool v16_ok = (uintptr_t)(x + m0) % 16 == 0;
+  auto win = [&](int l) {  // window-origin pointer of the staged d_l
+    return S + a.woff[L + 1 - l] + ((-fe<K>(l)) & (V - 1));
+  };
+  if (L == 1) {
+    idwt_level1<T, K, kFThreads>(S + a.woff[0], S + a.woff[1], x + m0, v16_ok, C >> 1, h, g,
+                                 threadIdx.x);
+    return;
+  }
+  // passes of at most 64 units run on warp 0 alone; the block waits for
+  // them before its next pass
+  bool warp0_wrote = false;
+  auto phase = [&](int units) {
+    if (units <= 64) {
+      warp0_wrote = true;
+      return threadIdx.x < 32 ? 1 : 0;  // 1: warp 0 runs it, 0: skip
+    }
+    if (warp0_wrote) __syncthreads();
+    warp0_wrote = false;
+    return 2;  // the whole block
+  };
+  const T* Aw = S + a.woff[0] + ((-fe<K>(L)) & (V - 1));  // a_L
   int l = L;
-  // coarse levels >= 2 (at most 64 pairs of the chunk): warp 0 alone
-  if (l >= 2 && (C >> l) <= 64) {
-    if (threadIdx.x < 32) {
-      const T* A2 = Acur;
-      int doff2 = doff;
-      for (int l2 = l; l2 >= 2 && (C >> l2) <= 64; --l2) {
-        const int em = s_e[l2 - 1];
-        const T* D = S + doff2 + ((-s_e[l2]) & (V - 1));
-        doff2 += fidwt_seg_cap<T, K>(l2);
-        T* B = ((l2 - 1) & 1) ? P1 : P0;
-        idwt_level<T, K, 32>(A2, D, B, (C >> l2) + (em + 1) / 2, -(em & 1), h, g, threadIdx.x);
+  if (L & 1) {  // an odd number of levels: level L alone first
+    const int em = fe<K>(L - 1);
+    const int np = (C >> L) + (em + 1) / 2;
+    T* B = P(L - 1);
+    const int ph = phase((np + 1) / 2);
+    if (ph == 1) {
+      idwt_level<T, K, 32>(Aw, win(L), B, np, h, g, threadIdx.x);
+      __syncwarp();
+    } else if (ph == 2) {
+      idwt_level<T, K, kFThreads>(Aw, win(L), B, np, h, g, threadIdx.x);
+      __syncthreads();
+    }
+    Aw = B + (em & 1);
+    l = L - 1;
+  }
+  for (; l >= 4; l -= 2) {
+    const int e2 = fe<K>(l - 2);
+    const bool odd = fe<K>(l - 1) & 1;
+    const int units = ((C >> (l - 1)) + (e2 + 1) / 2 + 3) / 4;
+    T* B = P(l - 2);
+    const int ph = phase(units);
+    if (ph != 0) {
+      if (ph == 1) {
+        if (odd) idwt_pair<T, K, 32, true>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
+        else idwt_pair<T, K, 32, false>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
         __syncwarp();
-        A2 = B;
+      } else {
+        if (odd)
+          idwt_pair<T, K, kFThreads, true>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
+        else
+          idwt_pair<T, K, kFThreads, false>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
+        __syncthreads();
       }
     }
-    // every thread advances to the first fine level
-    for (; l >= 2 && (C >> l) <= 64; --l) {
-      doff += fidwt_seg_cap<T, K>(l);
-      Acur = ((l - 1) & 1) ? P1 : P0;
-    }
-    __syncthreads();
+    Aw = B + (e2 & 1);
   }
-  // fine levels >= 2: the whole block
-  for (; l >= 2; --l) {
-    const int em = s_e[l - 1];
-    const T* D = S + doff + ((-s_e[l]) & (V - 1));
-    doff += fidwt_seg_cap<T, K>(l);
-    T* B = ((l - 1) & 1) ? P1 : P0;
-    idwt_level<T, K, kFThreads>(Acur, D, B, (C >> l) + (em + 1) / 2, -(em & 1), h, g,
-                                threadIdx.x);
-    __syncthreads();
-    Acur = B;
-  }
-  // level 1: C/2 pairs, straight to the output (doff is the d_1 window)
-  const bool v16_ok = (uintptr_t)(x + m0) % 16 == 0;
-  if (L == 1)
-    idwt_level1<T, K, true, kFThreads>(S, S + doff, x + m0, v16_ok, C >> 1, h, g, threadIdx.x);
+  if (warp0_wrote) __syncthreads();
+  // levels 2 and 1 to the output
+  if (L == 2)
+    idwt_pair_last<T, K, kFThreads, true>(S + a.woff[0], S + a.woff[1], S + a.woff[2], x + m0,
+                                          v16_ok, C >> 1, h, g, threadIdx.x);
   else
-    idwt_level1<T, K, false, kFThreads>(Acur, S + doff, x + m0, v16_ok, C >> 1, h, g,
-                                        threadIdx.x);
+    idwt_pair_last<T, K, kFThreads, false>(P(2), S + a.woff[L - 1], S + a.woff[L], x + m0, v16_ok,
+                                           C >> 1, h, g, threadIdx.x);
 }
 
 template <typename T, int K>
 size_t filter_smem(bool fwd, int L) {
   const int elems = fwd ? fdwt_cap_a<T, K>(L) + fdwt_cap_b<T, K>(L)
-                        : fidwt_stage_cap<T, K>(L) + fidwt_seg_cap<T, K>(1) + fidwt_seg_cap<T, K>(2);
+                        : fidwt_stage_cap<T, K>(L) + fidwt_big_cap<T, K>() + fidwt_small_cap<T, K>();
   return (size_t)elems * sizeof(T);
 }
 
