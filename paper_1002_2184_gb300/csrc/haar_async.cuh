@@ -40,9 +40,12 @@ __device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s,
   const int sh = (int)(s & (V - 1));  // s mod V, also for negative s (two's complement)
   const bool vec = ((uintptr_t)row % 16 == 0) && (P % V == 0) && s >= 0 && s + cnt <= P;
   if (vec) {
-    const T* src = row + (s - sh);
+    // one 32-bit shared and one global address, both advanced per copy
+    const T* src = row + (s - sh) + tid * V;
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst) + tid * 16u;
     const int nv = (sh + cnt + V - 1) / V;
-    for (int i = tid; i < nv; i += NT) cp_async16(dst + i * V, src + i * V);
+    for (int i = tid; i < nv; i += NT, src += NT * V, d += NT * 16u)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
   } else {
     for (int i = tid; i < cnt; i += NT) {
       int64_t gpos = (s + i) % P;

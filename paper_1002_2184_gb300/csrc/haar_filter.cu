@@ -445,15 +445,39 @@ __device__ __forceinline__ void idwt_pair(const T* Aw, const T* Dw, const T* Dw1
   }
 }
 
+// 8 consecutive output values at a unit's start, whose alignment is that of
+// the chunk start (units are 8 values, chunks 4096): one 256-bit store (AL =
+// 32), 16-byte stores (AL = 16) or element stores (AL = 0).
+template <typename T, int AL>
+__device__ __forceinline__ void put8(T* p, const T (&y)[8]) {
+  if constexpr (AL == 32 && sizeof(T) == 4) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(y[0]),
+                 "f"(y[1]), "f"(y[2]), "f"(y[3]), "f"(y[4]), "f"(y[5]), "f"(y[6]), "f"(y[7])
+                 : "memory");
+  } else if constexpr (AL == 32) {
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(y[0]), "d"(y[1]),
+                 "d"(y[2]), "d"(y[3])
+                 : "memory");
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 4), "d"(y[4]), "d"(y[5]),
+                 "d"(y[6]), "d"(y[7])
+                 : "memory");
+  } else if constexpr (AL == 16) {
+    store4(p, y);
+    store4(p + 4, y + 4);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) p[i] = y[i];
+  }
+}
+
 // The last pass (levels 2 and 1), straight to the output.  Every window
 // shift is a compile-time constant here (e_1 and e_2 depend on K only), so
 // a_2 and d_2 come in 2-element and d_1 in 16-byte aligned vectors from the
 // buffer starts Ab, D2b, D1b.  a_2 sits in the big buffer (shift e_2 mod 2)
 // or, for two levels, in its staged window.
-template <typename T, int K, int NT, bool A_STAGED>
+template <typename T, int K, int NT, bool A_STAGED, int AL>
 __device__ __forceinline__ void idwt_pair_last(const T* Ab, const T* D2b, const T* D1b, T* xo,
-                                               bool v_ok, int np1, const T* h, const T* g,
-                                               int tid) {
+                                               int np1, const T* h, const T* g, int tid) {
   using V2 = typename FVec2<T>::type;
   using VT = typename FVec16<T>::type;
   constexpr int V = fvec<T>();
@@ -493,8 +517,8 @@ __device__ __forceinline__ void idwt_pair_last(const T* Ab, const T* D2b, const 
     T y[8];
     syn_unit<T, K, ODD>(av, dv, d1, h, g, y);
     T* xp = xo + 8 * u;
-    if (v_ok && 4 * u + 3 < np1) {
-      store8(xp, y);  // whole sectors where the address allows
+    if (4 * u + 3 < np1) {
+      put8<T, AL>(xp, y);
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -508,9 +532,9 @@ __device__ __forceinline__ void idwt_pair_last(const T* Ab, const T* D2b, const 
 
 // One level alone (a single-level transform): a thread makes 4 pairs from
 // the staged a_1 and d_1 windows (shift (-HL) mod V for both).
-template <typename T, int K, int NT>
-__device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, bool v16_ok, int np,
-                                            const T* h, const T* g, int tid) {
+template <typename T, int K, int NT, int AL>
+__device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, int np, const T* h,
+                                            const T* g, int tid) {
   using VT = typename FVec16<T>::type;
   constexpr int V = fvec<T>();
   constexpr int HL = K / 2 - 1;
@@ -538,8 +562,8 @@ __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, boo
       y[2 * k + 1] = o;
     }
     T* xp = xo + 8 * p;
-    if (v16_ok && 4 * p + 3 < np) {
-      store8(xp, y);
+    if (4 * p + 3 < np) {
+      put8<T, AL>(xp, y);
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -587,13 +611,15 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   }
   cp_async_wait_all();
   __syncthreads();
-  const bool v16_ok = (uintptr_t)(x + m0) % 16 == 0;
+  const int al = (uintptr_t)(x + m0) % 32 == 0 ? 32 : (uintptr_t)(x + m0) % 16 == 0 ? 16 : 0;
   auto win = [&](int l) {  // window-origin pointer of the staged d_l
     return S + a.woff[L + 1 - l] + ((-fe<K>(l)) & (V - 1));
   };
   if (L == 1) {
-    idwt_level1<T, K, kFThreads>(S + a.woff[0], S + a.woff[1], x + m0, v16_ok, C >> 1, h, g,
-                                 threadIdx.x);
+    const T *A1 = S + a.woff[0], *D1 = S + a.woff[1];
+    if (al == 32) idwt_level1<T, K, kFThreads, 32>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else if (al == 16) idwt_level1<T, K, kFThreads, 16>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else idwt_level1<T, K, kFThreads, 0>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
     return;
   }
   // passes of at most 64 units run on warp 0 alone; the block waits for
@@ -648,12 +674,23 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   }
   if (warp0_wrote) __syncthreads();
   // levels 2 and 1 to the output
-  if (L == 2)
-    idwt_pair_last<T, K, kFThreads, true>(S + a.woff[0], S + a.woff[1], S + a.woff[2], x + m0,
-                                          v16_ok, C >> 1, h, g, threadIdx.x);
-  else
-    idwt_pair_last<T, K, kFThreads, false>(P(2), S + a.woff[L - 1], S + a.woff[L], x + m0, v16_ok,
-                                           C >> 1, h, g, threadIdx.x);
+  if (L == 2) {
+    const T *Ab = S + a.woff[0], *D2 = S + a.woff[1], *D1 = S + a.woff[2];
+    if (al == 32)
+      idwt_pair_last<T, K, kFThreads, true, 32>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else if (al == 16)
+      idwt_pair_last<T, K, kFThreads, true, 16>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else
+      idwt_pair_last<T, K, kFThreads, true, 0>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+  } else {
+    const T *Ab = P(2), *D2 = S + a.woff[L - 1], *D1 = S + a.woff[L];
+    if (al == 32)
+      idwt_pair_last<T, K, kFThreads, false, 32>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else if (al == 16)
+      idwt_pair_last<T, K, kFThreads, false, 16>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else
+      idwt_pair_last<T, K, kFThreads, false, 0>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+  }
 }
 
 template <typename T, int K>
