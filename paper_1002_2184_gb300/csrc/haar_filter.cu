@@ -13,15 +13,16 @@
 //   x[2n + p] = sum_i h[p + 2i] a[n - i] + g[p + 2i] d[n - i],  i < K/2.
 //
 // Work is cut into chunks of 4096 level-0 positions (4096 / 2^l coefficients
-// at level l).  Analysis: the chunk plus a right halo of (K - 2)(2^L - 1)
-// samples (wrapped) is staged in shared memory with asynchronous 16-byte
-// copies and every level is fused there, two levels per pass: a thread takes
-// 8 consecutive inputs of level l, makes 4 outputs of level l + 1 (and the
-// K - 2 low-pass ones after them) in registers and from those 2 outputs of
-// level l + 2, so level l + 1 never touches shared memory.  Synthesis: a_L and the window of
-// every d_l the chunk needs (K/2 - 1 extra coefficients per level on the
-// left) are staged in one go, the levels run coarsest first and level 1 is
-// written straight to the output.
+// at level l; 8192 for the analysis with K >= 6).  Analysis: the chunk plus
+// a right halo of (K - 2)(2^L - 1) samples (wrapped) is staged in shared
+// memory with asynchronous 16-byte copies and every level is fused there,
+// two levels per pass: a thread takes 8 consecutive inputs of level l, makes
+// 4 outputs of level l + 1 (and the K - 2 low-pass ones after them) in
+// registers and from those 2 outputs of level l + 2, so level l + 1 never
+// touches shared memory.  Synthesis: a_L and the window of every d_l the
+// chunk needs (K/2 - 1 extra coefficients per level on the left) are staged
+// in one go and the levels run coarsest first, also two per pass; the last
+// pass (levels 2 and 1) writes the output.
 #include <cuda_runtime.h>
 
 #include "fasthaar.h"
@@ -35,7 +36,14 @@ constexpr int kFChunk = 4096;  // level-0 positions per block
 constexpr int kFMaxLevels = 10;
 constexpr int kFMaxTaps = 8;
 constexpr int kFThreads = 128;   // synthesis block
-constexpr int kFThreadsA = 128;  // analysis block
+
+// Analysis chunk and block.  A chunk recomputes a right halo of
+// (K - 2)(2^L - 1) samples for its coarser levels, so the longer filters
+// take chunks twice as long (the same 32 samples per thread).
+template <int K>
+__host__ __device__ constexpr int fchunk_a() { return K >= 6 ? 8192 : 4096; }
+template <int K>
+__host__ __device__ constexpr int fthreads_a() { return K >= 6 ? 256 : 128; }
 
 struct FilterArgs {
   const void* in;
@@ -65,11 +73,11 @@ __host__ __device__ constexpr int fround(int v, int m) { return (v + m - 1) / m 
 // bytes of slack for the reads past the end
 template <typename T, int K>
 __host__ __device__ constexpr int fdwt_cap_a(int L) {
-  return fround(kFChunk + (K - 2) * ((1 << L) - 1) + 2 * fvec<T>(), fvec<T>());
+  return fround(fchunk_a<K>() + (K - 2) * ((1 << L) - 1) + 2 * fvec<T>(), fvec<T>());
 }
 template <typename T, int K>
 __host__ __device__ constexpr int fdwt_cap_b(int L) {
-  return fround(kFChunk / 4 + (K - 2) * ((1 << L) - 1) / 4 + 2 * fvec<T>(), fvec<T>());
+  return fround(fchunk_a<K>() / 4 + (K - 2) * ((1 << L) - 1) / 4 + 2 * fvec<T>(), fvec<T>());
 }
 // synthesis: the window of level l (a_l or d_l) spans (chunk >> l) + at most
 // 2 (K/2 - 1) + 1 positions; every window is staged with a 16-byte slack and
@@ -164,7 +172,7 @@ __device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half
 // len/4) are computed from the buffer's slack and not stored: the last unit
 // reads up to X[len + r + 5] (fp32) or X[len + r + 3] (fp64), inside the
 // 2 * 16 bytes of slack every staging buffer has.
-template <typename T, int K>
+template <typename T, int K, bool DETAILS = true>
 __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T* g, T (&e1)[4],
                                           T (&a2)[2], T (&e2)[2]) {
   using VT = typename FVec16<T>::type;
@@ -182,12 +190,14 @@ __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T
     for (int k = 0; k < K; ++k) s = fma(h[k], x[2 * j + k], s);
     a1[j] = s;
   }
+  if constexpr (DETAILS) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    T s = T(0);
+    for (int j = 0; j < 4; ++j) {
+      T s = T(0);
 #pragma unroll
-    for (int k = 0; k < K; ++k) s = fma(g[k], x[2 * j + k], s);
-    e1[j] = s;
+      for (int k = 0; k < K; ++k) s = fma(g[k], x[2 * j + k], s);
+      e1[j] = s;
+    }
   }
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -195,7 +205,7 @@ __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       s = fma(h[k], a1[2 * j + k], s);
-      d = fma(g[k], a1[2 * j + k], d);
+      if constexpr (DETAILS) d = fma(g[k], a1[2 * j + k], d);
     }
     a2[j] = s;
     e2[j] = d;
@@ -226,15 +236,20 @@ __device__ __forceinline__ void dwt_pair(const T* X, T* lo, T* d1, T* d2, int le
   const int n1 = len >> 1, n2 = len >> 2;
   for (int u = nfull + tid; 2 * u < m2; u += NT) {
     T e1[4], a2[2], e2[2];
-    pair_unit<T, K>(X, u, h, g, e1, a2, e2);
+    if (4 * u < n1) {  // a ragged chunk's last unit, or any unit without VEC
+      pair_unit<T, K>(X, u, h, g, e1, a2, e2);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (4 * u + i < n1) d1[4 * u + i] = e1[i];
+      for (int i = 0; i < 4; ++i)
+        if (4 * u + i < n1) d1[4 * u + i] = e1[i];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      if (2 * u + i < n2) d2[2 * u + i] = e2[i];
-      if (2 * u + i < m2) lo[2 * u + i] = a2[i];
+      for (int i = 0; i < 2; ++i)
+        if (2 * u + i < n2) d2[2 * u + i] = e2[i];
+    } else {  // a halo unit: only its low-pass outputs are kept
+      pair_unit<T, K, false>(X, u, h, g, e1, a2, e2);
     }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      if (2 * u + i < m2) lo[2 * u + i] = a2[i];
   }
 }
 
@@ -256,7 +271,8 @@ __device__ __forceinline__ void dwt_pair_step(const T* X, T* Y, T* out, T* d1, T
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kFThreadsA) k_filter_dwt(const FilterArgs a) {
+__global__ void __launch_bounds__(fthreads_a<K>()) k_filter_dwt(const FilterArgs a) {
+  constexpr int NT = fthreads_a<K>(), CH = fchunk_a<K>();
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -270,14 +286,14 @@ __global__ void __launch_bounds__(kFThreadsA) k_filter_dwt(const FilterArgs a) {
     g[k] = param<T>(a.g[k], a.gf[k]);
   }
   const unsigned chunks = (unsigned)a.chunks;
-  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kFChunk;
+  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * CH;
   const int64_t n = a.n;
-  const int C = (int)min((int64_t)kFChunk, n - k0);
+  const int C = (int)min((int64_t)CH, n - k0);
   T* out = static_cast<T*>(a.out) + row * n;
   // the chunk and the (K - 2)(2^L - 1) samples to its right that the coarser
   // levels' filters reach; k0 is a multiple of 16 bytes, so no shift
   int r = (K - 2) * ((1 << L) - 1);
-  stage<kFThreadsA>(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x);
+  stage<NT>(A, static_cast<const T*>(a.in) + row * n, n, k0, C + r, threadIdx.x);
   cp_async_wait_all();
   __syncthreads();
   T* X = A;
@@ -293,7 +309,7 @@ __global__ void __launch_bounds__(kFThreadsA) k_filter_dwt(const FilterArgs a) {
     T* lo = out + (k0 >> L);
     const bool last = l + 2 == L;
     if (!solo && (m2 + 1) / 2 > 64) {
-      dwt_pair_step<T, K, kFThreadsA>(X, Y, lo, d1, d2, last, len, m2, h, g, threadIdx.x);
+      dwt_pair_step<T, K, NT>(X, Y, lo, d1, d2, last, len, m2, h, g, threadIdx.x);
       __syncthreads();
     } else {
       // at most 64 units: warp 0 alone, the other warps are done
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(kFThreadsA) k_filter_dwt(const FilterArgs a) {
     T* lo = out + (k0 >> L);
     T* dl = out + (n >> L) + (k0 >> L);
     if (!solo && half > 64) {
-      dwt_level<T, K, kFThreadsA>(X, lo, dl, half, half, h, g, threadIdx.x);
+      dwt_level<T, K, NT>(X, lo, dl, half, half, h, g, threadIdx.x);
     } else if (threadIdx.x < 32) {
       dwt_level<T, K, 32>(X, lo, dl, half, half, h, g, threadIdx.x);
     }
@@ -701,14 +717,19 @@ size_t filter_smem(bool fwd, int L) {
 }
 
 template <typename T, int K>
-cudaError_t filter_launch_k(bool fwd, const FilterArgs& a, int64_t total, cudaStream_t s) {
+cudaError_t filter_launch_k(bool fwd, FilterArgs a, cudaStream_t s) {
+  const int chunk = fwd ? fchunk_a<K>() : kFChunk;
+  a.chunks = (a.n + chunk - 1) / chunk;
+  const int64_t total = a.rows * a.chunks;
+  if (total == 0) return cudaSuccess;
+  if (total > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const size_t smem = filter_smem<T, K>(fwd, a.levels);
   auto kern = fwd ? k_filter_dwt<T, K> : k_filter_idwt<T, K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)total);
-  cfg.blockDim = dim3(fwd ? kFThreadsA : kFThreads);
+  cfg.blockDim = dim3(fwd ? fthreads_a<K>() : kFThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -742,15 +763,11 @@ cudaError_t window_offsets(FilterArgs& a, int K) {
 
 template <typename T>
 cudaError_t filter_launch(bool fwd, FilterArgs a, int K, cudaStream_t s) {
-  a.chunks = (a.n + kFChunk - 1) / kFChunk;
-  const int64_t total = a.rows * a.chunks;
-  if (total == 0) return cudaSuccess;
-  if (total > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   switch (K) {
-    case 2: return filter_launch_k<T, 2>(fwd, a, total, s);
-    case 4: return filter_launch_k<T, 4>(fwd, a, total, s);
-    case 6: return filter_launch_k<T, 6>(fwd, a, total, s);
-    case 8: return filter_launch_k<T, 8>(fwd, a, total, s);
+    case 2: return filter_launch_k<T, 2>(fwd, a, s);
+    case 4: return filter_launch_k<T, 4>(fwd, a, s);
+    case 6: return filter_launch_k<T, 6>(fwd, a, s);
+    case 8: return filter_launch_k<T, 8>(fwd, a, s);
   }
   return cudaErrorInvalidValue;
 }
