@@ -69,15 +69,15 @@ __host__ __device__ constexpr int fround(int v, int m) { return (v + m - 1) / m 
 
 // ---- shared-memory footprints (host and device agree on these) ----
 // analysis: staged window (chunk + right halo) and one quarter-size buffer
-// for a_2, a_6, ... (a_4, a_8, ... go back to the first); both with 2 * 16
-// bytes of slack for the reads past the end
+// for a_2, a_6, ... (a_4, a_8, ... go back to the first); both with 16
+// elements of slack for the reads past the end
 template <typename T, int K>
 __host__ __device__ constexpr int fdwt_cap_a(int L) {
-  return fround(fchunk_a<K>() + (K - 2) * ((1 << L) - 1) + 2 * fvec<T>(), fvec<T>());
+  return fround(fchunk_a<K>() + (K - 2) * ((1 << L) - 1) + 16, fvec<T>());
 }
 template <typename T, int K>
 __host__ __device__ constexpr int fdwt_cap_b(int L) {
-  return fround(fchunk_a<K>() / 4 + (K - 2) * ((1 << L) - 1) / 4 + 2 * fvec<T>(), fvec<T>());
+  return fround(fchunk_a<K>() / 4 + (K - 2) * ((1 << L) - 1) / 4 + 16, fvec<T>());
 }
 // synthesis: the window of level l (a_l or d_l) spans (chunk >> l) + at most
 // 2 (K/2 - 1) + 1 positions; every window is staged with a 16-byte slack and
@@ -163,15 +163,16 @@ __device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half
   }
 }
 
-// Two levels in one pass.  X holds this level's input: len samples of the
-// chunk and a right halo r; m2 = len/4 + r2 outputs of level l + 2 are made
+// Two levels in one pass, a thread per unit (the form for K <= 4).  X holds
+// this level's input: len samples of the chunk and a right halo r; m2 =
+// len/4 + r2 outputs of level l + 2 are made
 // (r2 = (r - 3(K - 2)) / 4, the halo the levels after it need).  Unit u reads
 // X[8u, 8u + 3K + 2): a_{l+1}[4u + j] for j < K + 2 (the last K - 2 belong to
 // the next unit as well and are made twice), d_{l+1}[4u + j] for j < 4, then
 // a_{l+2} and d_{l+2} at 2u and 2u + 1.  Outputs past the ends (m2, len/2,
 // len/4) are computed from the buffer's slack and not stored: the last unit
 // reads up to X[len + r + 5] (fp32) or X[len + r + 3] (fp64), inside the
-// 2 * 16 bytes of slack every staging buffer has.
+// 16 elements of slack every staging buffer has.
 template <typename T, int K, bool DETAILS = true>
 __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T* g, T (&e1)[4],
                                           T (&a2)[2], T (&e2)[2]) {
@@ -217,7 +218,7 @@ __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T
 // whose only stored outputs are a_{l+2}, and the last unit of a ragged
 // chunk -- store one by one under guards.
 template <typename T, int K, int NT, bool VEC>
-__device__ __forceinline__ void dwt_pair(const T* X, T* lo, T* d1, T* d2, int len, int m2,
+__device__ __forceinline__ void dwt_pair_rc(const T* X, T* lo, T* d1, T* d2, int len, int m2,
                                          const T* h, const T* g, int tid) {
   using V2 = typename FVec2<T>::type;
   const int nfull = VEC ? len >> 3 : 0;
@@ -251,6 +252,109 @@ __device__ __forceinline__ void dwt_pair(const T* X, T* lo, T* d1, T* d2, int le
     for (int i = 0; i < 2; ++i)
       if (2 * u + i < m2) lo[2 * u + i] = a2[i];
   }
+}
+
+// Two levels in one pass, a warp at a time (the form for K >= 6, where the
+// values made twice above are most of the work).  X holds this level's
+// input: len samples of the chunk and a right halo r; m2 = len/4 + r2
+// outputs of level l + 2 are made (r2 = (r - 3(K - 2)) / 4, the halo the
+// levels after it need) by U = ceil(m2 / 2) units.  Unit u makes a_{l+1}[4u + j] and
+// d_{l+1}[4u + j] (j < 4) from X[8u, 8u + K + 6), then a_{l+2} and d_{l+2} at
+// 2u, 2u + 1, which also read a_{l+1}[4u + 4, 4u + K + 2): the first values
+// of units u + 1 and u + 2, taken from the next lanes with shuffles.  A warp
+// pass covers W = 32 - R units; its last R = ceil((K - 2) / 4) lanes only
+// make values for their neighbours.  Outputs past the ends (m2, len/2, len/4)
+// come from the buffer's slack and are not stored; lanes past the last unit
+// read as the R-th lane after it, so reads end at X[len + r + 9], inside the
+// 16 elements of slack every staging buffer has.  Units u < len/8 have all
+// their outputs inside: with VEC (every output vector aligned) a pass of such
+// units stores whole vectors without guards.
+template <typename T, int K, int NT, bool VEC>
+__device__ __forceinline__ void dwt_pair_sh(const T* X, T* lo, T* d1, T* d2, int len, int m2,
+                                         const T* h, const T* g, int tid) {
+  using VT = typename FVec16<T>::type;
+  using V2 = typename FVec2<T>::type;
+  constexpr int V = fvec<T>();
+  constexpr int R = (K - 2 + 3) / 4;
+  constexpr int W = 32 - R;
+  constexpr int NW = (K + 6 + V - 1) / V;  // 16-byte loads per unit
+  const int lane = tid & 31;
+  const int U = (m2 + 1) / 2, n1 = len >> 1, n2 = len >> 2;
+  const int nfull = VEC ? len >> 3 : 0;
+  for (int base = (tid >> 5) * W; base < U; base += (NT / 32) * W) {
+    const int u = base + lane;
+    const int ur = min(u, U - 1 + R);
+    T x[NW * V];
+#pragma unroll
+    for (int i = 0; i < NW; ++i)
+      *reinterpret_cast<VT*>(x + i * V) = reinterpret_cast<const VT*>(X + 8 * ur)[i];
+    // a pass past len/8 units keeps no details (halo units feed the coarser
+    // levels' low-pass outputs only); the same for the whole warp
+    const bool details = 4 * base < n1;
+    T a1[K + 2], e1[4] = {}, e2[2] = {}, a2[2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s = fma(h[k], x[2 * j + k], s);
+      a1[j] = s;
+    }
+    if (details) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) s = fma(g[k], x[2 * j + k], s);
+        e1[j] = s;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K - 2; ++j) a1[4 + j] = __shfl_down_sync(0xffffffffu, a1[j % 4], 1 + j / 4);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s = fma(h[k], a1[2 * j + k], s);
+      a2[j] = s;
+    }
+    if (details) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        T d = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) d = fma(g[k], a1[2 * j + k], d);
+        e2[j] = d;
+      }
+    }
+    if (lane < W) {
+      if (base + W <= nfull) {
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4*>(d1 + 4 * u) = make_float4(e1[0], e1[1], e1[2], e1[3]);
+        } else {
+          *reinterpret_cast<V2*>(d1 + 4 * u) = V2{e1[0], e1[1]};
+          *reinterpret_cast<V2*>(d1 + 4 * u + 2) = V2{e1[2], e1[3]};
+        }
+        *reinterpret_cast<V2*>(d2 + 2 * u) = V2{e2[0], e2[1]};
+        *reinterpret_cast<V2*>(lo + 2 * u) = V2{a2[0], a2[1]};
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (4 * u + i < n1) d1[4 * u + i] = e1[i];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (2 * u + i < n2) d2[2 * u + i] = e2[i];
+          if (2 * u + i < m2) lo[2 * u + i] = a2[i];
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int K, int NT, bool VEC>
+__device__ __forceinline__ void dwt_pair(const T* X, T* lo, T* d1, T* d2, int len, int m2,
+                                         const T* h, const T* g, int tid) {
+  if constexpr (K >= 6) dwt_pair_sh<T, K, NT, VEC>(X, lo, d1, d2, len, m2, h, g, tid);
+  else dwt_pair_rc<T, K, NT, VEC>(X, lo, d1, d2, len, m2, h, g, tid);
 }
 
 // One step on NT threads: the low-pass outputs go to shared memory (Y) or,

@@ -20,7 +20,12 @@ TAPS = {"haar": tuple(np.full(2, 1 / np.sqrt(2.0))), "d4": tuple(_d4()),
 
 @pytest.mark.parametrize("name", list(TAPS))
 @pytest.mark.parametrize("rows,n,levels", [(1, 64, 3), (3, 4096, 6), (2, 6144, 10),
-                                           (1, 1 << 16, 4), (2, 1024, 10), (1, 16, 4)])
+                                           (1, 1 << 16, 4), (2, 1024, 10), (1, 16, 4),
+                                           # one or two levels (a single pass), odd and even
+                                           # level counts, full chunks followed by a ragged one
+                                           # (4096- and 8192-sample chunks)
+                                           (3, 4096, 1), (2, 8192, 2), (1, 2048, 5),
+                                           (2, 4096 + 256, 7), (2, 10240, 9), (1, 12288, 8)])
 @pytest.mark.parametrize("dt", [torch.float32, torch.float64])
 def test_filter_bank_matches_oracle(name, rows, n, levels, dt):
     h = TAPS[name]
