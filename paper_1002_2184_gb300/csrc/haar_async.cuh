@@ -28,24 +28,43 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// Copy n elements from src to dst, both 16-byte aligned, as ceil(n / V)
+// 16-byte pieces shared by NT threads (one 32-bit shared and one global
+// address, both advanced per copy).
+template <int NT, typename T>
+__device__ __forceinline__ void stage_span(T* dst, const T* src, int n, int tid) {
+  constexpr int V = fvec<T>();
+  src += tid * V;
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst) + tid * 16u;
+  const int nv = (n + V - 1) / V;
+  for (int i = tid; i < nv; i += NT, src += NT * V, d += NT * 16u)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // Stage positions [s, s + cnt) of a sequence of period P stored at `row`
-// into dst[sh + i], sh = s mod (16 / sizeof(T)).  Inside the sequence and
-// with a 16-byte aligned row the copy is made of aligned 16-byte pieces
-// (which may also bring a few neighbours, inside [0, P)); otherwise, e.g. for
-// windows that wrap around, each element is copied on its own.  Returns sh.
-// NT: the number of threads sharing the copy (a compile-time stride).
+// into dst[sh + i], sh = s mod (16 / sizeof(T)).  With a 16-byte aligned row
+// and P a multiple of 16 bytes, the window is a run [s mod P, P) followed by
+// whole periods and a last partial run from 0 (a window longer than the
+// period wraps several times), and each run is copied in aligned 16-byte
+// pieces (which may also bring a few neighbours, inside [0, P)): every run
+// after the first starts at dst[sh + done] with done = P - (s mod P) + a
+// multiple of P, a multiple of 16 bytes.  Windows of more than 8 periods, or
+// unaligned rows, copy each element on its own.  Returns sh.  NT: the number
+// of threads sharing the copy (a compile-time stride).
 template <int NT, typename T>
 __device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s, int cnt, int tid) {
   constexpr int V = fvec<T>();
   const int sh = (int)(s & (V - 1));  // s mod V, also for negative s (two's complement)
-  const bool vec = ((uintptr_t)row % 16 == 0) && (P % V == 0) && s >= 0 && s + cnt <= P;
-  if (vec) {
-    // one 32-bit shared and one global address, both advanced per copy
-    const T* src = row + (s - sh) + tid * V;
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst) + tid * 16u;
-    const int nv = (sh + cnt + V - 1) / V;
-    for (int i = tid; i < nv; i += NT, src += NT * V, d += NT * 16u)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  if ((uintptr_t)row % 16 == 0 && P % V == 0 && cnt <= 8 * P) {
+    int64_t s0 = s % P;
+    if (s0 < 0) s0 += P;
+    int done = (int)min((int64_t)cnt, P - s0);
+    stage_span<NT>(dst, row + (s0 - sh), sh + done, tid);
+    while (done < cnt) {
+      const int len = (int)min((int64_t)(cnt - done), P);
+      stage_span<NT>(dst + sh + done, row, len, tid);
+      done += len;
+    }
   } else {
     for (int i = tid; i < cnt; i += NT) {
       int64_t gpos = (s + i) % P;

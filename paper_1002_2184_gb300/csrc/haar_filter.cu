@@ -54,6 +54,7 @@ struct FilterArgs {
   double h[kFMaxTaps], g[kFMaxTaps];
   float hf[kFMaxTaps], gf[kFMaxTaps];  // the same, rounded once on the host
   int woff[kFMaxLevels + 2];           // synthesis: offset of staged window w (a_L, d_L, ..., d_1)
+  int e[kFMaxLevels + 1];              // synthesis: e_l of the window starts (host-computed)
 };
 
 template <typename T> struct FVec2;
@@ -725,7 +726,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int w = warp; w <= L; w += kFThreads / 32) {
       const int l = w == 0 ? L : L + 1 - w;
-      const int64_t nl = n >> l, s = (m0 >> l) - fe<K>(l);
+      const int64_t nl = n >> l, s = (m0 >> l) - a.e[l];
       stage<32>(S + a.woff[w], w == 0 ? c : c + nl, nl, s, (int)((end >> l) - s), lane);
     }
   }
@@ -733,7 +734,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   __syncthreads();
   const int al = (uintptr_t)(x + m0) % 32 == 0 ? 32 : (uintptr_t)(x + m0) % 16 == 0 ? 16 : 0;
   auto win = [&](int l) {  // window-origin pointer of the staged d_l
-    return S + a.woff[L + 1 - l] + ((-fe<K>(l)) & (V - 1));
+    return S + a.woff[L + 1 - l] + ((-a.e[l]) & (V - 1));
   };
   if (L == 1) {
     const T *A1 = S + a.woff[0], *D1 = S + a.woff[1];
@@ -754,10 +755,10 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     warp0_wrote = false;
     return 2;  // the whole block
   };
-  const T* Aw = S + a.woff[0] + ((-fe<K>(L)) & (V - 1));  // a_L
+  const T* Aw = S + a.woff[0] + ((-a.e[L]) & (V - 1));  // a_L
   int l = L;
   if (L & 1) {  // an odd number of levels: level L alone first
-    const int em = fe<K>(L - 1);
+    const int em = a.e[L - 1];
     const int np = (C >> L) + (em + 1) / 2;
     T* B = P(L - 1);
     const int ph = phase((np + 1) / 2);
@@ -772,8 +773,8 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     l = L - 1;
   }
   for (; l >= 4; l -= 2) {
-    const int e2 = fe<K>(l - 2);
-    const bool odd = fe<K>(l - 1) & 1;
+    const int e2 = a.e[l - 2];
+    const bool odd = a.e[l - 1] & 1;
     const int units = ((C >> (l - 1)) + (e2 + 1) / 2 + 3) / 4;
     T* B = P(l - 2);
     const int ph = phase(units);
@@ -844,7 +845,8 @@ cudaError_t filter_launch_k(bool fwd, FilterArgs a, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-// Offsets of the synthesis windows a_L, d_L, ..., d_1 in the staging area.
+// Offsets of the synthesis windows a_L, d_L, ..., d_1 in the staging area,
+// and the e_l of their starts.
 template <typename T, int K>
 void window_offsets_k(FilterArgs& a) {
   int off = 0;
@@ -853,6 +855,7 @@ void window_offsets_k(FilterArgs& a) {
     a.woff[w] = off;
     off += fidwt_seg_cap<T, K>(l);
   }
+  for (int l = 0; l <= a.levels; ++l) a.e[l] = fe<K>(l);
 }
 template <typename T>
 cudaError_t window_offsets(FilterArgs& a, int K) {

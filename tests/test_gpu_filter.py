@@ -55,3 +55,27 @@ def test_filter_rejections():
         == _lib.HAAR_EALIAS
     assert lib.haar_filter_dwt_1d(x.data_ptr(), y.data_ptr(), 0, 2, 96, 11, h4, 4, st) \
         == _lib.HAAR_EINVAL
+
+
+@pytest.mark.parametrize("name", ["d4", "lattice8"])
+def test_filter_bank_full_size_rows(name):
+    """The benchmark's shape (64 signals of 2^20 fp32 samples, 8 levels: 256
+    or 128 chunks per row, every chunk seam and the deepest halo): two whole
+    rows against the oracle, coefficient by coefficient and through the
+    inverse, and the round trip of every row."""
+    h = TAPS[name]
+    rows, n, levels = 64, 1 << 20, 8
+    base = torch.from_numpy(np.stack([synth.signal_1d(n, seed=7, index=i) for i in range(4)]))
+    x = base.to(DEV).float().repeat(rows // 4, 1)
+    x[5] *= -0.5  # rows 5 and 62 differ from the repeated ones
+    x[62] = torch.flip(x[62], [0])
+    c = api.filter_dwt1d(x, levels, h)
+    y = api.filter_idwt1d(c, levels, h)
+    for r in (5, 62):
+        xr = x[r].double().cpu().numpy()
+        ref = oracle.filter_dwt1d(xr[None], levels, np.array(h))[0]
+        assert oracle.rel_l2(c[r].double().cpu().numpy(), ref) <= 1e-6
+        yref = oracle.filter_idwt1d(c[r].double().cpu().numpy()[None], levels, np.array(h))[0]
+        assert oracle.rel_l2(y[r].double().cpu().numpy(), yref) <= 1e-6
+    err = torch.linalg.vector_norm((y - x).double(), dim=1) / torch.linalg.vector_norm(x.double(), dim=1)
+    assert float(err.max()) <= 1e-6
