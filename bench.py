@@ -685,10 +685,25 @@ def signal_batch_form(api, synth, dev):
             "denoise_bytes_per_sample": 8}
 
 
+def lattice_taps(angles):
+    """An orthonormal low-pass of length 2 * len(angles) from a paraunitary
+    lattice of plane rotations and two-sample delays (each stage keeps the
+    double-shift orthogonality the bank's perfect reconstruction needs)."""
+    c, s = np.cos(angles[0]), np.sin(angles[0])
+    h0, h1 = np.array([c, s]), np.array([-s, c])
+    for th in angles[1:]:
+        c, s = np.cos(th), np.sin(th)
+        a, b = np.concatenate([h0, [0.0, 0.0]]), np.concatenate([[0.0, 0.0], h1])
+        h0, h1 = c * a + s * b, -s * a + c * b
+    return tuple(float(v) for v in h0)
+
+
 def filter_form(api, synth, dev):
     """The same polyphase bank with longer orthonormal low-pass filters:
-    64 x 2^20 fp32 signals, 8 levels, DWT + IDWT, K = 2 (Haar) and 4
-    (Daubechies-4) through the general K-tap kernels."""
+    64 x 2^20 fp32 signals, 8 levels, DWT + IDWT, K = 2 (Haar), 4
+    (Daubechies-4) and 8 (a lattice filter) through the general K-tap
+    kernels; the round trip and each direction alone (back-to-back
+    launches)."""
     import torch
     rows, n, L = 64, 1 << 20, 8
     base = [torch.from_numpy(synth.signal_1d(n, synth.Signal1D.seed, i).astype(np.float32))
@@ -698,13 +713,30 @@ def filter_form(api, synth, dev):
     y = torch.empty_like(x)
     px = rows * n
     out = {"workload": f"{rows} x 2^20 fp32 signals, {L} levels, DWT + IDWT, periodic"}
-    for name, taps in (("haar_k2", api.HAAR2), ("daubechies4_k4", api.DAUBECHIES4)):
+    for name, taps in (("haar_k2", api.HAAR2), ("daubechies4_k4", api.DAUBECHIES4),
+                       ("lattice_k8", lattice_taps([0.2, 0.5, -0.4, 0.9]))):
         ms = time_ms(lambda: (api.filter_dwt1d(x, L, taps, out=c),
                               api.filter_idwt1d(c, L, taps, out=y)), 20)
         ok = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)) <= 1e-6
+        dwt_ms = time_ms(lambda: api.filter_dwt1d(x, L, taps, out=c), 20)
+        idwt_ms = time_ms(lambda: api.filter_idwt1d(c, L, taps, out=y), 20)
         out[name] = {"ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
                      "frac_of_hbm": round(16.0 * px / (ms * 1e-3) / 1e9 / _hbm(), 4),
+                     "dwt_frac_of_hbm": round(8.0 * px / (dwt_ms * 1e-3) / 1e9 / _hbm(), 4),
+                     "idwt_frac_of_hbm": round(8.0 * px / (idwt_ms * 1e-3) / 1e9 / _hbm(), 4),
                      "round_trip_ok": ok}
+    # short rows: 16384 signals of 4096 samples, one chunk each, so every
+    # staged window wraps around its row
+    xs = x.reshape(-1, 4096)
+    cs, ys = c.reshape(-1, 4096), y.reshape(-1, 4096)
+    taps = api.DAUBECHIES4
+    dwt_ms = time_ms(lambda: api.filter_dwt1d(xs, L, taps, out=cs), 20)
+    idwt_ms = time_ms(lambda: api.filter_idwt1d(cs, L, taps, out=ys), 20)
+    ok = float(torch.linalg.vector_norm(ys - xs) / torch.linalg.vector_norm(xs)) <= 1e-6
+    out["daubechies4_k4_16384x4096"] = {
+        "dwt_frac_of_hbm": round(8.0 * px / (dwt_ms * 1e-3) / 1e9 / _hbm(), 4),
+        "idwt_frac_of_hbm": round(8.0 * px / (idwt_ms * 1e-3) / 1e9 / _hbm(), 4),
+        "round_trip_ok": ok}
     return out
 
 
