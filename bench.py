@@ -555,8 +555,14 @@ def forms(api, synth, dev, world):
 
         ms = time_ms(rt, 5, warmup=2)
         nbytes = px * (x.element_size() + 2 * c.element_size() + y.element_size())
+        dwt_ms = time_ms(plan.dwt, 5, warmup=2)
+        idwt_ms = time_ms(plan.idwt, 5, warmup=2)
         entry[name] = {"ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
-                       "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1)}
+                       "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                       "dwt_gbs": round(px * (x.element_size() + c.element_size())
+                                        / (dwt_ms * 1e-3) / 1e9, 1),
+                       "idwt_gbs": round(px * (c.element_size() + y.element_size())
+                                         / (idwt_ms * 1e-3) / 1e9, 1)}
         del x, c, y, plan
     for name in ("bf16", "fp16", "u8_in_bf16_coef_fp32_out"):
         entry[name]["speedup_vs_fp32"] = round(entry["fp32"]["ms"] / entry[name]["ms"], 3)
