@@ -56,8 +56,11 @@ __device__ __forceinline__ int stage(T* dst, const T* row, int64_t P, int64_t s,
   constexpr int V = fvec<T>();
   const int sh = (int)(s & (V - 1));  // s mod V, also for negative s (two's complement)
   if ((uintptr_t)row % 16 == 0 && P % V == 0 && cnt <= 8 * P) {
-    int64_t s0 = s % P;
-    if (s0 < 0) s0 += P;
+    int64_t s0 = s < 0 ? s + P : s;  // windows start at most one period early
+    if (s0 < 0 || s0 >= P) {         // any other start: a 64-bit remainder
+      s0 = s % P;
+      if (s0 < 0) s0 += P;
+    }
     int done = (int)min((int64_t)cnt, P - s0);
     stage_span<NT>(dst, row + (s0 - sh), sh + done, tid);
     while (done < cnt) {
