@@ -17,9 +17,10 @@
 // a right halo of (K - 2)(2^L - 1) samples (wrapped) is staged in shared
 // memory with asynchronous 16-byte copies and every level is fused there,
 // two levels per pass: a thread takes 8 consecutive inputs of level l, makes
-// 4 outputs of level l + 1 (and the K - 2 low-pass ones after them) in
-// registers and from those 2 outputs of level l + 2, so level l + 1 never
-// touches shared memory.  Synthesis: a_L and the window of every d_l the
+// 4 outputs of level l + 1 in registers (and the K - 2 low-pass ones after
+// them: made again for K <= 4, taken from the next lanes for K >= 6) and
+// from those 2 outputs of level l + 2, so level l + 1 never touches shared
+// memory.  Synthesis: a_L and the window of every d_l the
 // chunk needs (K/2 - 1 extra coefficients per level on the left) are staged
 // in one go and the levels run coarsest first, also two per pass; the last
 // pass (levels 2 and 1) writes the output.
@@ -32,7 +33,7 @@
 
 namespace fh {
 
-constexpr int kFChunk = 4096;  // level-0 positions per block
+constexpr int kFChunk = 4096;  // level-0 positions per synthesis block
 constexpr int kFMaxLevels = 10;
 constexpr int kFMaxTaps = 8;
 constexpr int kFThreads = 128;   // synthesis block
@@ -166,14 +167,14 @@ __device__ __forceinline__ void dwt_level(const T* A, T* lo_dst, T* dl, int half
 
 // Two levels in one pass, a thread per unit (the form for K <= 4).  X holds
 // this level's input: len samples of the chunk and a right halo r; m2 =
-// len/4 + r2 outputs of level l + 2 are made
-// (r2 = (r - 3(K - 2)) / 4, the halo the levels after it need).  Unit u reads
-// X[8u, 8u + 3K + 2): a_{l+1}[4u + j] for j < K + 2 (the last K - 2 belong to
-// the next unit as well and are made twice), d_{l+1}[4u + j] for j < 4, then
-// a_{l+2} and d_{l+2} at 2u and 2u + 1.  Outputs past the ends (m2, len/2,
-// len/4) are computed from the buffer's slack and not stored: the last unit
-// reads up to X[len + r + 5] (fp32) or X[len + r + 3] (fp64), inside the
-// 16 elements of slack every staging buffer has.
+// len/4 + r2 outputs of level l + 2 are made (r2 = (r - 3(K - 2)) / 4, the
+// halo the levels after it need).  Unit u reads X[8u, 8u + 3K + 2):
+// a_{l+1}[4u + j] for j < K + 2 (the last K - 2 belong to the next unit as
+// well and are made twice), d_{l+1}[4u + j] for j < 4, then a_{l+2} and
+// d_{l+2} at 2u and 2u + 1.  Outputs past the ends (m2, len/2, len/4) are
+// computed from the buffer's slack and not stored: the last unit reads up
+// to X[len + r + 5] (fp32) or X[len + r + 3] (fp64), inside the 16 elements
+// of slack every staging buffer has.
 template <typename T, int K, bool DETAILS = true>
 __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T* g, T (&e1)[4],
                                           T (&a2)[2], T (&e2)[2]) {
@@ -220,7 +221,7 @@ __device__ __forceinline__ void pair_unit(const T* X, int u, const T* h, const T
 // chunk -- store one by one under guards.
 template <typename T, int K, int NT, bool VEC>
 __device__ __forceinline__ void dwt_pair_rc(const T* X, T* lo, T* d1, T* d2, int len, int m2,
-                                         const T* h, const T* g, int tid) {
+                                            const T* h, const T* g, int tid) {
   using V2 = typename FVec2<T>::type;
   const int nfull = VEC ? len >> 3 : 0;
   for (int u = tid; u < nfull; u += NT) {
@@ -259,20 +260,21 @@ __device__ __forceinline__ void dwt_pair_rc(const T* X, T* lo, T* d1, T* d2, int
 // values made twice above are most of the work).  X holds this level's
 // input: len samples of the chunk and a right halo r; m2 = len/4 + r2
 // outputs of level l + 2 are made (r2 = (r - 3(K - 2)) / 4, the halo the
-// levels after it need) by U = ceil(m2 / 2) units.  Unit u makes a_{l+1}[4u + j] and
-// d_{l+1}[4u + j] (j < 4) from X[8u, 8u + K + 6), then a_{l+2} and d_{l+2} at
-// 2u, 2u + 1, which also read a_{l+1}[4u + 4, 4u + K + 2): the first values
-// of units u + 1 and u + 2, taken from the next lanes with shuffles.  A warp
-// pass covers W = 32 - R units; its last R = ceil((K - 2) / 4) lanes only
-// make values for their neighbours.  Outputs past the ends (m2, len/2, len/4)
-// come from the buffer's slack and are not stored; lanes past the last unit
-// read as the R-th lane after it, so reads end at X[len + r + 9], inside the
-// 16 elements of slack every staging buffer has.  Units u < len/8 have all
-// their outputs inside: with VEC (every output vector aligned) a pass of such
-// units stores whole vectors without guards.
+// levels after it need) by U = ceil(m2 / 2) units.  Unit u makes
+// a_{l+1}[4u + j] and d_{l+1}[4u + j] (j < 4) from X[8u, 8u + K + 6), then
+// a_{l+2} and d_{l+2} at 2u, 2u + 1, which also read a_{l+1}[4u + 4,
+// 4u + K + 2): the first values of units u + 1 and u + 2, taken from the
+// next lanes with shuffles.  A warp pass covers W = 32 - R units; its last
+// R = ceil((K - 2) / 4) lanes only make values for their neighbours.
+// Outputs past the ends (m2, len/2, len/4) come from the buffer's slack and
+// are not stored; lanes past the last unit read as the R-th lane after it,
+// so reads end at X[len + r + 9], inside the 16 elements of slack every
+// staging buffer has.  Units u < len/8 have all their outputs inside: with
+// VEC (every output vector aligned) a pass of such units stores whole
+// vectors without guards.
 template <typename T, int K, int NT, bool VEC>
 __device__ __forceinline__ void dwt_pair_sh(const T* X, T* lo, T* d1, T* d2, int len, int m2,
-                                         const T* h, const T* g, int tid) {
+                                            const T* h, const T* g, int tid) {
   using VT = typename FVec16<T>::type;
   using V2 = typename FVec2<T>::type;
   constexpr int V = fvec<T>();
