@@ -134,3 +134,26 @@ def test_volume_beyond_2_31_voxels():
     torch.cuda.synchronize()
     err = float((y[1, -2:] - x[1, -2:]).abs().max())
     assert err <= 1e-5
+
+
+def test_filter_bank_beyond_2_31_samples():
+    """The K-tap bank on 2049 rows of 2^20 samples (2,148,532,224 > 2^31;
+    Daubechies-4, 8 levels): the last rows, whose offsets need 64 bits, are
+    whole rows the oracle can take, checked coefficient by coefficient and
+    through the round trip."""
+    import oracle
+    from paper_1002_2184_gb300 import api
+    rows, n, L = 2049, 1 << 20, 8
+    assert rows * n > 2 ** 31
+    if _free_gb() < 3 * rows * n * 4 / 2**30 + 2:
+        pytest.skip("needs ~26 GB of free device memory")
+    h = api.DAUBECHIES4
+    x = _seeded((rows, n), 13)
+    c = api.filter_dwt1d(x, L, h)
+    y = api.filter_idwt1d(c, L, h)
+    torch.cuda.synchronize()
+    for r in (2047, 2048):
+        xr = x[r].double().cpu().numpy()
+        ref = oracle.filter_dwt1d(xr[None], L, np.array(h))[0]
+        assert oracle.rel_l2(c[r].double().cpu().numpy(), ref) <= 1e-6, r
+        assert float((y[r] - x[r]).abs().max()) <= 1e-5, r
