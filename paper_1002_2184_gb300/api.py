@@ -101,7 +101,26 @@ def _out_like(x: torch.Tensor, dtype: torch.dtype, out: Optional[torch.Tensor]) 
         return torch.empty(x.shape, dtype=dtype, device=x.device)
     if out.shape != x.shape:
         raise ValueError(f"out has shape {tuple(out.shape)}, expected {tuple(x.shape)}")
+    if out.device != x.device:
+        raise ValueError(f"out is on {out.device}, the input on {x.device}")
     return out
+
+
+def _check_same_type(what: str, src: torch.Tensor, out: torch.Tensor, shape) -> None:
+    """For the entry points that take one element type and plain pointers for
+    both buffers: out must have the given shape, src's dtype and device, and
+    both must be contiguous CUDA tensors (checked before the library is
+    called, so a mismatch never reaches a kernel)."""
+    if tuple(out.shape) != tuple(shape):
+        raise ValueError(f"{what}: out has shape {tuple(out.shape)}, expected {tuple(shape)}")
+    if out.dtype != src.dtype:
+        raise ValueError(f"{what}: out has dtype {out.dtype}, the input {src.dtype}")
+    if not (src.is_contiguous() and out.is_contiguous()):
+        raise ValueError(f"{what} needs contiguous tensors")
+    if out.device != src.device:
+        raise ValueError(f"{what}: out is on {out.device}, the input on {src.device}")
+    if not src.is_cuda:
+        raise ValueError("libfasthaar works on CUDA tensors only")
 
 
 def _coef_dtype(x: torch.Tensor, dtype: Optional[torch.dtype]) -> torch.dtype:
@@ -313,12 +332,11 @@ def denoise2d(x: torch.Tensor, levels: int, threshold: float, hard: bool = False
 def swt1d(x: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Undecimated Haar transform of every row of (..., n) (contiguous):
     returns (..., levels + 1, n) with [a_L, d_1, ..., d_L]."""
-    if not x.is_contiguous():
-        raise ValueError("swt1d needs a contiguous input")
     n = x.shape[-1]
     rows = x.numel() // max(n, 1)
     shape = tuple(x.shape[:-1]) + (levels + 1, n)
     out = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else out
+    _check_same_type("swt1d", x, out, shape)
     lib = _lib.load()
     with torch.cuda.device(x.device):
         rc = lib.haar_swt_1d(x.data_ptr(), out.data_ptr(), haar_dtype(x.dtype), rows, n, levels,
@@ -329,12 +347,14 @@ def swt1d(x: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None) -> t
 
 def iswt1d(c: torch.Tensor, levels: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Inverse of :func:`swt1d`."""
-    if not c.is_contiguous():
-        raise ValueError("iswt1d needs a contiguous input")
     n = c.shape[-1]
+    if c.dim() < 2 or c.shape[-2] != levels + 1:
+        raise ValueError(f"iswt1d: coefficients of shape (..., {levels + 1}, n) expected, "
+                         f"got {tuple(c.shape)}")
     shape = tuple(c.shape[:-2]) + (n,)
     rows = c.numel() // max((levels + 1) * n, 1)
     out = torch.empty(shape, dtype=c.dtype, device=c.device) if out is None else out
+    _check_same_type("iswt1d", c, out, shape)
     lib = _lib.load()
     with torch.cuda.device(c.device):
         rc = lib.haar_iswt_1d(c.data_ptr(), out.data_ptr(), haar_dtype(c.dtype), rows, n, levels,
@@ -394,8 +414,7 @@ HAAR2 = (2.0 ** -0.5, 2.0 ** -0.5)
 
 
 def _filter_call(fn_name, src, dst, levels, taps):
-    if not (src.is_contiguous() and dst.is_contiguous()):
-        raise ValueError("filter transforms need contiguous tensors")
+    _check_same_type(fn_name, src, dst, src.shape)
     n = src.shape[-1]
     rows = src.numel() // max(n, 1)
     arr = (ctypes.c_double * len(taps))(*taps)
