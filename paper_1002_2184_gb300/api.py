@@ -168,6 +168,9 @@ class Plan:
 
     def __init__(self, x: torch.Tensor, coef: torch.Tensor, levels: int,
                  y: Optional[torch.Tensor] = None, one_d: bool = False):
+        for t in (coef, y):
+            if t is not None and t.device != x.device:
+                raise ValueError(f"Plan: a buffer is on {t.device}, the input on {x.device}")
         self.lib = _lib.load()
         self.levels = int(levels)
         self.device = x.device

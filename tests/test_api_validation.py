@@ -47,3 +47,9 @@ def test_out_on_another_device_is_rejected():
         api.dwt2d(x, 2, out=torch.empty(2, 64, 64, device="meta"))
     with pytest.raises(ValueError, match="meta"):
         api.filter_dwt1d(torch.zeros(2, 64), 2, out=torch.empty(2, 64, device="meta"))
+
+
+def test_plan_rejects_buffers_on_another_device():
+    x = torch.zeros(2, 64, 64)
+    with pytest.raises(ValueError, match="meta"):
+        api.Plan(x, torch.empty(2, 64, 64, device="meta"), 2)
