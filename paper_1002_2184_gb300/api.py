@@ -229,6 +229,8 @@ class RaggedPlan:
         self.lib = _lib.load()
         self.items = [(int(h), int(w), int(L)) for h, w, L in items]
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:  # "cuda": the current GPU
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.unit, self.blocks_per_sm = int(unit), int(blocks_per_sm)
         offs, o = [], 0
         for h, w, _ in self.items:
@@ -270,6 +272,8 @@ class RaggedPlan:
     def _run(self, fn, src: torch.Tensor, dst: torch.Tensor, stream=None):
         if src.numel() < self.numel or dst.numel() < self.numel:
             raise ValueError("buffer smaller than the plan's layout")
+        if src.device != self.device or dst.device != self.device:
+            raise ValueError(f"ragged buffers must be on the plan's device {self.device}")
         if not (src.is_contiguous() and dst.is_contiguous()):
             raise ValueError("ragged buffers must be contiguous")
         st = (torch.cuda.current_stream(self.device).cuda_stream if stream is None
