@@ -250,9 +250,14 @@ int haar_ragged_plan_destroy(haar_ragged_plan *plan);
  * Mallat layout [a_L | d_L | ... | d_1]:
  *   a[n] = sum_k h[k] x[(2n+k) mod N],   d[n] = sum_k g[k] x[(2n+k) mod N],
  *   g[k] = (-1)^(k+1) h[K-1-k]   (K = 2 gives the Haar detail sign of Eq. 9).
- * Only the decimated outputs are computed.  x, coef: rows x n contiguous,
- * F32 or F64; n divisible by 2^levels; 1 <= levels <= 10; `lowpass` is a
- * host array of ntaps doubles (orthonormality is the caller's to ensure). */
+ * Only the decimated outputs are computed.  x, coef: device pointers owned
+ * by the caller, rows x n contiguous elements of the one type `dtype` (F32 or
+ * F64, else HAAR_EDTYPE), not overlapping (HAAR_EALIAS); n divisible by
+ * 2^levels (HAAR_ESHAPE); 1 <= levels <= 10, ntaps in {2, 4, 6, 8}, non-null
+ * pointers (HAAR_EINVAL); `lowpass` is a
+ * host array of ntaps doubles, read before the call returns (orthonormality
+ * is the caller's to ensure).  Asynchronous on the stream; a launch failure
+ * returns HAAR_ECUDA.  rows == 0 or n == 0 is a no-op. */
 int haar_filter_dwt_1d(const void *x, void *coef, int dtype, int64_t rows, int64_t n, int levels,
                        const double *lowpass, int ntaps, void *cuda_stream);
 int haar_filter_idwt_1d(const void *coef, void *x, int dtype, int64_t rows, int64_t n,
@@ -267,8 +272,12 @@ int haar_filter_idwt_1d(const void *coef, void *x, int dtype, int64_t rows, int6
  * It is the direct form whose decimated outputs the Fast Haar bank never
  * computes: d_l[2^l m] and a_L[2^L m] are the decimated transform's
  * coefficients.  x: rows x n contiguous; coef: rows x (levels + 1) x n
- * contiguous, row 0 = a_L, row l = d_l.  F32 or F64; 1 <= levels <= 10;
- * n >= 2^levels.  The inverse averages the two reconstructions of each
+ * contiguous, row 0 = a_L, row l = d_l; both device pointers owned by the
+ * caller, of the one type `dtype` (F32 or F64, else HAAR_EDTYPE), not
+ * overlapping (HAAR_EALIAS); 1 <= levels <= 10 and non-null pointers
+ * (HAAR_EINVAL); n >= 2^levels (HAAR_ESHAPE: a dilated tap would wrap more
+ * than once); rows == 0 or n == 0 is a no-op; asynchronous on the stream,
+ * HAAR_ECUDA if the launch fails.  The inverse averages the two reconstructions of each
  * sample: a_{l-1}[k] = ((a_l[k] - d_l[k]) + (a_l[k-s] + d_l[k-s])) / (2 sqrt 2). */
 int haar_swt_1d(const void *x, void *coef, int dtype, int64_t rows, int64_t n, int levels,
                 void *cuda_stream);
