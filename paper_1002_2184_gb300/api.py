@@ -420,6 +420,37 @@ DAUBECHIES4 = tuple(v / (4.0 * 2.0 ** 0.5) for v in (1 + _R3, 3 + _R3, 3 - _R3, 
 HAAR2 = (2.0 ** -0.5, 2.0 ** -0.5)
 
 
+def daubechies(ntaps: int) -> Tuple[float, ...]:
+    """Daubechies' orthonormal low-pass with ntaps / 2 vanishing moments
+    (ntaps in {2, 4, 6, 8}: the lengths the K-tap kernels take), by the
+    spectral factorisation of Daubechies' construction: with N = ntaps / 2,
+    |m0(w)|^2 = cos^(2N)(w/2) Q(sin^2(w/2)), Q(y) = sum_{k<N} C(N-1+k, k) y^k;
+    substituting y = -(z - 1)^2 / (4z) makes z^(N-1) Q a polynomial in z
+    whose roots come in pairs r, 1/r, and the filter is (1 + z)^N times the
+    factor with the roots inside the unit circle (minimum phase), scaled to
+    sum(h) = sqrt(2).  ntaps = 2 gives HAAR2 and 4 gives DAUBECHIES4."""
+    import numpy as np
+    from math import comb
+    if ntaps not in (2, 4, 6, 8):
+        raise ValueError("ntaps must be 2, 4, 6 or 8")
+    n = ntaps // 2
+    poly = np.zeros(1)
+    for k in range(n):
+        term = np.array([comb(n - 1 + k, k) * (-0.25) ** k])
+        for _ in range(k):
+            term = np.polymul(term, [1.0, -2.0, 1.0])  # (z - 1)^2
+        term = np.polymul(term, np.r_[1.0, np.zeros(n - 1 - k)])  # z^(n-1-k)
+        poly = np.polyadd(poly, term)
+    h = np.array([1.0])
+    if n > 1:
+        roots = np.roots(poly)
+        h = np.real(np.poly(roots[np.abs(roots) < 1.0]))
+    for _ in range(n):
+        h = np.polymul(h, [1.0, 1.0])
+    h = h * (2.0 ** 0.5) / h.sum()
+    return tuple(float(v) for v in h)
+
+
 def _filter_call(fn_name, src, dst, levels, taps):
     _check_same_type(fn_name, src, dst, src.shape)
     n = src.shape[-1]

@@ -15,7 +15,8 @@ DEV = torch.device("cuda", 0)
 
 TAPS = {"haar": tuple(np.full(2, 1 / np.sqrt(2.0))), "d4": tuple(_d4()),
         "lattice6": tuple(lattice_lowpass([0.3, -0.7, 1.1])),
-        "lattice8": tuple(lattice_lowpass([0.2, 0.5, -0.4, 0.9]))}
+        "lattice8": tuple(lattice_lowpass([0.2, 0.5, -0.4, 0.9])),
+        "db6": api.daubechies(6), "db8": api.daubechies(8)}
 
 
 @pytest.mark.parametrize("name", list(TAPS))
