@@ -7,6 +7,7 @@ import torch
 
 import oracle
 from paper_1002_2184_gb300 import _lib, api, synth
+from parity_util import assert_close
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -31,24 +32,22 @@ def test_3d_matches_oracle(shape, levels, dt):
     x = volume(shape, seed=levels, dtype=dt)
     c = api.dwt3d(x, levels)
     ref = oracle.dwt3d(x.double().cpu().numpy(), levels)
-    tol = 1e-6 if dt == torch.float32 else 1e-2
-    assert oracle.rel_l2(c.double().cpu().numpy(), ref) <= tol
+    assert_close(c, ref, dt, f"dwt3d {shape} L{levels}")
     y = api.idwt3d(c, levels)
     yref = oracle.idwt3d(c.double().cpu().numpy(), levels)
-    assert oracle.rel_l2(y.double().cpu().numpy(), yref) <= tol
+    assert_close(y, yref, dt, f"idwt3d {shape} L{levels}")
     if dt == torch.float32:
-        assert oracle.rel_l2(y.double().cpu().numpy(), x.double().cpu().numpy()) <= 1e-6
+        assert_close(y, x.double().cpu().numpy(), dt, f"3d round trip {shape} L{levels}")
 
 
 def test_3d_fp64_and_strided():
     x = volume((2, 8, 16, 64), seed=3, dtype=torch.float64)
     c = api.dwt3d(x, 3)
-    assert oracle.rel_l2(c.cpu().numpy(), oracle.dwt3d(x.cpu().numpy(), 3)) <= 1e-13
+    assert_close(c, oracle.dwt3d(x.cpu().numpy(), 3), torch.float64, "dwt3d fp64")
     big = volume((1, 12, 20, 160), seed=4)
     v = big[:, 2:10, 2:18, 32:96]   # plane stride 20*160, row stride 160
     cv = api.dwt3d(v, 3)
-    assert oracle.rel_l2(cv.double().cpu().numpy(), oracle.dwt3d(v.double().cpu().numpy(), 3)) \
-        <= 1e-6
+    assert_close(cv, oracle.dwt3d(v.double().cpu().numpy(), 3), torch.float32, "dwt3d strided")
 
 
 def test_3d_constant_exact_zero_detail():

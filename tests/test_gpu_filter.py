@@ -8,10 +8,18 @@ import torch
 
 import oracle
 from paper_1002_2184_gb300 import _lib, api, synth
+from parity_util import assert_bands_close_1d, assert_close
 from test_oracle_pins import _d4, lattice_lowpass
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
+
+def approximations(x: np.ndarray, levels: int, h) -> list:
+    """The oracle's a_0 = x, a_1, ..., a_levels (the input of each level)."""
+    n = x.shape[-1]
+    return [x] + [oracle.filter_dwt1d(x, l, np.array(h))[..., : n >> l]
+                  for l in range(1, levels + 1)]
+
 
 TAPS = {"haar": tuple(np.full(2, 1 / np.sqrt(2.0))), "d4": tuple(_d4()),
         "lattice6": tuple(lattice_lowpass([0.3, -0.7, 1.1])),
@@ -33,13 +41,16 @@ def test_filter_bank_matches_oracle(name, rows, n, levels, dt):
     x = torch.from_numpy(np.stack([synth.signal_1d(n, seed=n, index=i) for i in range(rows)]))
     x = x.to(DEV).to(dt)
     c = api.filter_dwt1d(x, levels, h)
-    ref = oracle.filter_dwt1d(x.double().cpu().numpy(), levels, np.array(h))
-    tol = 1e-6 if dt == torch.float32 else 1e-13
-    assert oracle.rel_l2(c.double().cpu().numpy(), ref) <= tol
+    xh = x.double().cpu().numpy()
+    ref = oracle.filter_dwt1d(xh, levels, np.array(h))
+    what = f"{name} dwt {rows}x{n} L{levels}"
+    assert_close(c, ref, dt, what)
+    # every band on its own, against the scale of the signal it came from
+    assert_bands_close_1d(c, ref, approximations(xh, levels, h), levels, dt, what)
     y = api.filter_idwt1d(c, levels, h)
     yref = oracle.filter_idwt1d(c.double().cpu().numpy(), levels, np.array(h))
-    assert oracle.rel_l2(y.double().cpu().numpy(), yref) <= tol
-    assert oracle.rel_l2(y.double().cpu().numpy(), x.double().cpu().numpy()) <= tol
+    assert_close(y, yref, dt, f"{name} idwt {rows}x{n} L{levels}")
+    assert_close(y, xh, dt, f"{name} round trip {rows}x{n} L{levels}")
 
 
 def test_filter_rejections():
@@ -75,8 +86,10 @@ def test_filter_bank_full_size_rows(name):
     for r in (5, 62):
         xr = x[r].double().cpu().numpy()
         ref = oracle.filter_dwt1d(xr[None], levels, np.array(h))[0]
-        assert oracle.rel_l2(c[r].double().cpu().numpy(), ref) <= 1e-6
+        assert_close(c[r], ref, torch.float32, f"{name} full-size row {r}")
+        assert_bands_close_1d(c[r], ref, approximations(xr, levels, h), levels, torch.float32,
+                              f"{name} full-size row {r}")
         yref = oracle.filter_idwt1d(c[r].double().cpu().numpy()[None], levels, np.array(h))[0]
-        assert oracle.rel_l2(y[r].double().cpu().numpy(), yref) <= 1e-6
+        assert_close(y[r], yref, torch.float32, f"{name} full-size inverse row {r}")
     err = torch.linalg.vector_norm((y - x).double(), dim=1) / torch.linalg.vector_norm(x.double(), dim=1)
     assert float(err.max()) <= 1e-6

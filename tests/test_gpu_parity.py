@@ -15,27 +15,11 @@ import torch
 
 import oracle
 from paper_1002_2184_gb300 import api, synth
+from parity_util import TOL, assert_close  # noqa: F401  (shared comparison rules)
 
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
-TOL = {
-    torch.float32: (1e-6, 4e-6),
-    torch.bfloat16: (1e-2, 2.0 ** -7),
-    torch.float16: (2e-3, 2.0 ** -9),
-    torch.float64: (1e-13, 1e-13),
-}
-
-
-def assert_close(gpu, ref, dtype, what=""):
-    got = gpu.detach().double().cpu().numpy()
-    rel_tol, abs_tol = TOL[dtype]
-    err = oracle.rel_l2(got, ref)
-    scale = float(np.max(np.abs(ref))) if ref.size else 0.0
-    mx = oracle.max_abs(got, ref)
-    assert err <= rel_tol, f"{what}: rel-L2 {err:.3e} > {rel_tol:.1e}"
-    assert mx <= abs_tol * max(scale, 1e-30), f"{what}: max-abs {mx:.3e} (scale {scale:.3e})"
-    return err, mx
 
 
 def dev(a: np.ndarray, dtype) -> torch.Tensor:

@@ -7,6 +7,7 @@ import torch
 
 import oracle
 from paper_1002_2184_gb300 import _lib, api, synth
+from parity_util import assert_close
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -19,13 +20,35 @@ def test_swt_matches_oracle(rows, n, levels, dt):
     x = torch.from_numpy(np.stack([synth.signal_1d(n, seed=n, index=i) for i in range(rows)]))
     x = x.to(DEV).to(dt)
     u = api.swt1d(x, levels)
-    ref = oracle.swt1d(x.double().cpu().numpy(), levels)
-    tol = 1e-6 if dt == torch.float32 else 1e-13
-    assert oracle.rel_l2(u.double().cpu().numpy(), ref) <= tol
+    xh = x.double().cpu().numpy()
+    ref = oracle.swt1d(xh, levels)
+    # level by level: d_l (row l) is scaled by its own input a_{l-1}, a_L by
+    # a_{L-1}, so an error confined to one level cannot hide in the others
+    for l in range(levels + 1):
+        lev = levels if l == 0 else l
+        src = xh if lev == 1 else oracle.swt1d(xh, lev - 1)[..., 0, :]
+        assert_close(u[..., l, :], ref[..., l, :], dt, f"swt row {l} {rows}x{n} L{levels}",
+                     scale=float(np.max(np.abs(src))))
     y = api.iswt1d(u, levels)
     yref = oracle.iswt1d(u.double().cpu().numpy(), levels)
-    assert oracle.rel_l2(y.double().cpu().numpy(), yref) <= tol
-    assert oracle.rel_l2(y.double().cpu().numpy(), x.double().cpu().numpy()) <= tol
+    assert_close(y, yref, dt, f"iswt {rows}x{n} L{levels}")
+    assert_close(y, xh, dt, f"swt round trip {rows}x{n} L{levels}")
+
+
+@pytest.mark.parametrize("rows,n,levels", [(2, 64, 1), (3, 2048, 4), (1, 5000, 7),
+                                           (2, 1024, 10)])
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_iswt_inconsistent_coefficients(rows, n, levels, dt):
+    """The inverse on coefficients that are not the transform of any signal
+    (independent random rows, as after shrinkage or noise): each level must
+    average the two estimates of a_{l-1}, as the oracle does.  Keeping only
+    one estimate agrees with the oracle on consistent input but not here."""
+    rng = np.random.default_rng(1000 + n + levels)
+    u = rng.standard_normal((rows, levels + 1, n))
+    ud = torch.from_numpy(u).to(DEV).to(dt)
+    y = api.iswt1d(ud, levels)
+    yref = oracle.iswt1d(ud.double().cpu().numpy(), levels)
+    assert_close(y, yref, dt, f"iswt inconsistent {rows}x{n} L{levels}")
 
 
 def test_swt_decimated_equals_fast_dwt_on_gpu():

@@ -361,6 +361,73 @@ def test_loss_limits():
     assert np.allclose(g, 2 * x / x.size, atol=1e-16)
 
 
+def _haar_2x2_from_bands(ll, hx, hy, hh):
+    """The 2 x 2 image whose one-level coefficients are the given bands: the
+    textbook Haar basis images (box, step along the width, step along the
+    height, checkerboard), each of norm 1 after the factor 1/2."""
+    box = np.array([[1.0, 1.0], [1.0, 1.0]])
+    step_x = np.array([[-1.0, 1.0], [-1.0, 1.0]])
+    step_y = np.array([[-1.0, -1.0], [1.0, 1.0]])
+    checker = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    return 0.5 * (ll * box + hx * step_x + hy * step_y + hh * checker)
+
+
+# The coefficients of the intermediate-threshold case below and what the
+# denoising loss (t = 0.05, lam = 1e-3) must give, derived by hand:
+#   c = [[LL, Hx], [Hy, HH]] = [[2, 0.3], [-0.2, 0.03]]
+#   soft threshold: s = [[1.95, 0.25], [-0.15, 0]] (LL and Hx shrink toward 0,
+#     the negative Hy shrinks toward 0 keeping its sign, HH < t vanishes)
+#   mse = |x_r - x|^2 / 4 = |s - c|^2 / 4 (Parseval) = (3 * 0.05^2 + 0.03^2) / 4
+#   l1 = (|0.25| + |-0.15| + 0) / 3 (three detail coefficients; LL excluded)
+#   gradient, mapped back to coefficients (W g): a coefficient above t
+#   contributes only lam * sign(s) / 3 if it is a detail, one below t
+#   contributes 2 c / 4: W g = [[0, lam/3], [-lam/3, 0.015]]
+_C_MID = (2.0, 0.3, -0.2, 0.03)
+_T_MID, _LAM_MID = 0.05, 1e-3
+_MSE_MID = (3 * 0.05 ** 2 + 0.03 ** 2) / 4
+_L1_MID = (0.25 + 0.15) / 3
+_WG_MID = np.array([[0.0, _LAM_MID / 3], [-_LAM_MID / 3, 0.015]])
+
+
+def pin_loss_at_intermediate_threshold(loss_fn, grad_fn):
+    x = _haar_2x2_from_bands(*_C_MID)[None, None]
+    if not np.allclose(oracle.dwt2d(x[0, 0], 1), [[2.0, 0.3], [-0.2, 0.03]], atol=1e-15):
+        return False
+    loss, mse, l1 = loss_fn(x, 1, _T_MID, _LAM_MID)
+    if not (abs(mse - _MSE_MID) < 1e-15 and abs(l1 - _L1_MID) < 1e-15
+            and abs(loss - (_MSE_MID + _LAM_MID * _L1_MID)) < 1e-15):
+        return False
+    wg = oracle.dwt2d(grad_fn(x, 1, _T_MID, _LAM_MID)[0, 0], 1)
+    return bool(np.allclose(wg, _WG_MID, atol=1e-15))
+
+
+def test_loss_closed_form_at_intermediate_threshold():
+    """Soft threshold between 0 and infinity, on coefficients of both signs
+    above and below it, with the loss and gradient derived by hand."""
+    assert pin_loss_at_intermediate_threshold(oracle.denoise_loss, oracle.denoise_loss_grad)
+
+
+@pytest.mark.parametrize("mistake", ["half_threshold", "no_sign", "details_only",
+                                     "hard_instead_of_soft"])
+def test_planted_soft_threshold_mistake_is_caught(mistake, monkeypatch):
+    wrong = {
+        "half_threshold": lambda c, t: np.sign(c) * np.maximum(np.abs(c) - t / 2, 0.0),
+        "no_sign": lambda c, t: np.maximum(np.abs(np.asarray(c, float)) - t, 0.0),
+        "details_only": None,
+        "hard_instead_of_soft": lambda c, t: np.where(np.abs(c) > t, c, 0.0),
+    }[mistake]
+    if wrong is None:
+        # threshold every coefficient but the low band (LL kept)
+        def wrong(c, t):
+            c = np.asarray(c, float)
+            out = np.sign(c) * np.maximum(np.abs(c) - t, 0.0)
+            out[..., 0, 0] = c[..., 0, 0]
+            return out
+    monkeypatch.setattr(oracle, "soft_threshold", wrong)
+    assert not pin_loss_at_intermediate_threshold(oracle.denoise_loss,
+                                                  oracle.denoise_loss_grad)
+
+
 # --------------------------------------------------------------------------
 # Mutation test: mistakes planted in (wrappers around) the oracle, on the
 # CPU, must each fail at least one pin.
@@ -479,6 +546,67 @@ def test_swt_is_shift_equivariant_energy_and_pr():
     e = e + np.sum(u[:, 0] ** 2, axis=-1) / 2.0 ** L
     assert np.allclose(e, np.sum(x ** 2, axis=-1), rtol=1e-13)
     assert np.allclose(oracle.iswt1d(u, L), x, atol=1e-13)
+
+
+def _frame_matrix(n, levels):
+    """The undecimated transform as a ((levels + 1) n) x n matrix, column i
+    the (pinned) forward transform of the unit impulse e_i."""
+    return np.stack([oracle.swt1d(np.eye(n)[i], levels).reshape(-1) for i in range(n)], axis=1)
+
+
+def pin_iswt_is_weighted_least_squares(iswt):
+    """The undecimated transform F is redundant: most coefficient arrays are
+    the transform of no signal.  With weights 2^-l on d_l and 2^-L on a_L the
+    energy identity above says F^T W F = I, so the inverse that averages the
+    two estimates of a_{l-1} at every level is the weighted least-squares
+    solution argmin_x sum_l w_l |F_l x - c_l|^2, computed here by numpy's
+    least-squares routine on the explicit matrix, on random (inconsistent)
+    coefficients."""
+    rng = synth.rng(12, 0)
+    for n, L in ((16, 1), (32, 3), (64, 5)):
+        F = _frame_matrix(n, L)
+        w = np.concatenate([np.full(n, 2.0 ** -L)] + [np.full(n, 2.0 ** -l)
+                                                      for l in range(1, L + 1)])
+        c = rng.standard_normal((L + 1, n))
+        sw = np.sqrt(w)
+        x_ls = np.linalg.lstsq(F * sw[:, None], c.reshape(-1) * sw, rcond=None)[0]
+        if not np.allclose(iswt(c, L), x_ls, atol=1e-12):
+            return False
+    return True
+
+
+def test_iswt_is_the_weighted_least_squares_inverse():
+    assert pin_iswt_is_weighted_least_squares(oracle.iswt1d)
+
+
+def test_iswt_single_detail_perturbation_closed_form():
+    """One level, one detail coefficient d_1[k] moved by delta: the two
+    estimates of x disagree at k (by -delta/sqrt 2) and at k + 1 (by
+    +delta/sqrt 2); their average moves x[k] by -delta/(2 sqrt 2) and
+    x[k + 1] by +delta/(2 sqrt 2) and nothing else (with wrap-around)."""
+    x = synth.signal_1d(64, seed=13)
+    for k, delta in ((10, 0.7), (63, -1.3)):
+        u = oracle.swt1d(x, 1)
+        u[1, k] += delta
+        d = oracle.iswt1d(u, 1) - x
+        expect = np.zeros(64)
+        expect[k] = -delta * S / 2
+        expect[(k + 1) % 64] = delta * S / 2
+        assert np.allclose(d, expect, atol=1e-14)
+
+
+def test_planted_iswt_mistake_is_caught():
+    """Keeping one estimate of a_{l-1} (from position k only) reconstructs
+    consistent coefficients exactly, but is not the least-squares inverse."""
+    def first_estimate_only(c, L):
+        a = np.asarray(c[0], float).copy()
+        for l in range(L, 0, -1):
+            a = (a - c[l]) * S
+        return a
+
+    x = synth.signal_1d(32, seed=14)
+    assert np.allclose(first_estimate_only(oracle.swt1d(x, 3), 3), x, atol=1e-13)
+    assert not pin_iswt_is_weighted_least_squares(first_estimate_only)
 
 
 # --------------------------------------------------------------------------
