@@ -140,8 +140,14 @@ int haar_idwt_2d(const haar_desc *coef, const haar_desc *x, int levels, void *wo
  *  - A transform whose scratch (haar_workspace_size(HAAR_OP_DWT_2D, ...))
  *    exceeds 4 MiB is rejected with HAAR_EWORKSPACE; use haar_dwt_2d.
  *  - The first call on each device looks the array's address up
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.  Call it with the stream's device current.
+ *    (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    Call it with the stream's device current.  Not supported on a device
+ *    that has been reset (cudaDeviceReset) after that first call: the kept
+ *    address would point at freed memory.
+ *  - Argument errors are reported as by haar_dwt_2d (both descriptors are
+ *    checked first); HAAR_EWORKSPACE only for a valid call whose scratch is
+ *    too large.
  *  - All calls on a device share the one array and it keeps the last call's
  *    contents (nothing in it needs to start at zero).  Calls whose kernels
  *    overlap in time on the GPU (different streams, not ordered) race on the

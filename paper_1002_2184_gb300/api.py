@@ -197,17 +197,21 @@ class Plan:
             return torch.cuda.current_stream(self.device).cuda_stream
         return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
+    # The library launches on the calling thread's current device: make it
+    # the plan's device for the call, whatever device is current outside.
     def dwt(self, stream=None) -> None:
-        rc = self._fwd(self._px, self._pc, self.levels, self._ws_ptr, self._ws_n,
-                       self._stream(stream))
+        with torch.cuda.device(self.device):
+            rc = self._fwd(self._px, self._pc, self.levels, self._ws_ptr, self._ws_n,
+                           self._stream(stream))
         if rc:
             _lib.check(rc, "dwt")
 
     def idwt(self, stream=None) -> None:
         if self._py is None:
             raise ValueError("plan has no synthesis output")
-        rc = self._inv(self._pc, self._py, self.levels, self._ws_ptr, self._ws_n,
-                       self._stream(stream))
+        with torch.cuda.device(self.device):
+            rc = self._inv(self._pc, self._py, self.levels, self._ws_ptr, self._ws_n,
+                           self._stream(stream))
         if rc:
             _lib.check(rc, "idwt")
 
@@ -278,8 +282,10 @@ class RaggedPlan:
             raise ValueError("ragged buffers must be contiguous")
         st = (torch.cuda.current_stream(self.device).cuda_stream if stream is None
               else getattr(stream, "cuda_stream", stream))
-        rc = fn(self._h, src.data_ptr(), haar_dtype(src.dtype), dst.data_ptr(),
-                haar_dtype(dst.dtype), self._ws.data_ptr(), self._ws_n, st)
+        # the persistent grid is sized from the current device's SM count
+        with torch.cuda.device(self.device):
+            rc = fn(self._h, src.data_ptr(), haar_dtype(src.dtype), dst.data_ptr(),
+                    haar_dtype(dst.dtype), self._ws.data_ptr(), self._ws_n, st)
         if rc:
             _lib.check(rc, "ragged transform")
         return dst

@@ -213,6 +213,15 @@ int check_workspace(const Workspace& ws, void* workspace, size_t bytes) {
 
 }  // namespace
 
+namespace fh {
+// The argument checks of haar_dwt_2d alone, for the allocation-free variant
+// (haar_noalloc.cu), which must report argument errors before it looks at
+// the scratch size.
+int validate_dwt_2d(const haar_desc* x, const haar_desc* coef, int levels, bool* empty) {
+  return validate(x, coef, levels, true, true, empty);
+}
+}  // namespace fh
+
 extern "C" {
 
 int haar_version(void) { return FASTHAAR_VERSION; }

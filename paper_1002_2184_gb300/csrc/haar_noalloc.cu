@@ -14,13 +14,23 @@
 // library's device code is loaded holds kScratchBytes of it until the process
 // exits.  Host code cannot use the symbol's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and remembers it.
+// (with that device current) and remembers it for the life of the process.
+// A device reset (cudaDeviceReset) unloads the module and frees the array;
+// the remembered address would then be stale, so this entry point must not
+// be used on a device after it has been reset.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "fasthaar.h"
 #include "haar_internal.h"
+
+namespace fh {
+// The argument checks of haar_dwt_2d (descriptors, dtype pair, divisibility,
+// aliasing) without any launch (haar_api.cu); *empty is set for an input
+// with no pixels.
+int validate_dwt_2d(const haar_desc* x, const haar_desc* coef, int levels, bool* empty);
+}  // namespace fh
 
 namespace {
 
@@ -37,8 +47,13 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 extern "C" int haar_dwt_2d_noalloc(const haar_desc* x, const haar_desc* coef, int levels,
                                    void* cuda_stream) {
+  // Both descriptors are checked before the scratch size, so a bad output
+  // descriptor is reported as such whatever the input's size.
+  bool empty = false;
+  int rc = fh::validate_dwt_2d(x, coef, levels, &empty);
+  if (rc != HAAR_OK || empty) return rc;
   size_t need = 0;
-  int rc = haar_workspace_size(HAAR_OP_DWT_2D, x, levels, &need);
+  rc = haar_workspace_size(HAAR_OP_DWT_2D, x, levels, &need);
   if (rc != HAAR_OK) return rc;
   if (need > kScratchBytes) return HAAR_EWORKSPACE;  // larger than the built-in array
 

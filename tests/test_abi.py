@@ -269,3 +269,24 @@ def test_volume_rejections(lib):
         assert run(fn, v(A, rs=32), v(B), 1) == L.HAAR_EINVAL            # row stride < w
         assert run(fn, v(A), v(B), 4) == L.HAAR_EWORKSPACE               # deep: needs scratch
         assert run(fn, v(A, b=0), v(B, b=0), 2) == L.HAAR_OK
+
+
+def test_noalloc_validates_both_descriptors_before_the_scratch_size(lib):
+    """The allocation-free 2D analysis reports a bad output descriptor as
+    such even when the input is too large for its built-in scratch; only a
+    valid call gets HAAR_EWORKSPACE.  No device work: every call fails
+    validation."""
+    from paper_1002_2184_gb300 import _lib as L
+
+    def noalloc(src, dst, levels):
+        return lib.haar_dwt_2d_noalloc(ctypes.byref(src), ctypes.byref(dst), levels, None)
+
+    n = 1 << 17  # 2^34 pixels: 7 levels need far more than the built-in 4 MiB
+    big = d(A, h=n, w=n)
+    far = 1 << 44
+    assert noalloc(big, d(far, h=n, w=n // 2), 7) == L.HAAR_EINVAL      # shape mismatch
+    assert noalloc(big, d(far, dt=3, h=n, w=n), 7) == L.HAAR_EDTYPE     # uint8 output
+    assert noalloc(big, d(A + 64, h=n, w=n), 7) == L.HAAR_EALIAS        # overlapping output
+    assert noalloc(big, d(far, h=n, w=n), 0) == L.HAAR_EINVAL           # level count
+    assert noalloc(big, d(far, h=n, w=n), 7) == L.HAAR_EWORKSPACE       # valid, too large
+    assert noalloc(d(A, b=0), d(B, b=0), 3) == L.HAAR_OK                # empty: nothing to do
