@@ -174,6 +174,7 @@ class Plan:
         self.lib = _lib.load()
         self.levels = int(levels)
         self.device = x.device
+        self._dev_index = x.device.index
         self._keep = (x, coef, y)
         self._dx = describe(x, one_d)
         self._dc = describe(coef, one_d)
@@ -197,23 +198,25 @@ class Plan:
             return torch.cuda.current_stream(self.device).cuda_stream
         return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
-    # The library launches on the calling thread's current device: make it
-    # the plan's device for the call, whatever device is current outside.
-    def dwt(self, stream=None) -> None:
-        with torch.cuda.device(self.device):
-            rc = self._fwd(self._px, self._pc, self.levels, self._ws_ptr, self._ws_n,
-                           self._stream(stream))
+    # The library launches on the calling thread's current device: the call
+    # is made with the plan's device current (switched only when another
+    # device is current, so the common case costs one device query).
+    def _call(self, fn, a, b, stream, what):
+        if torch.cuda.current_device() == self._dev_index:
+            rc = fn(a, b, self.levels, self._ws_ptr, self._ws_n, self._stream(stream))
+        else:
+            with torch.cuda.device(self.device):
+                rc = fn(a, b, self.levels, self._ws_ptr, self._ws_n, self._stream(stream))
         if rc:
-            _lib.check(rc, "dwt")
+            _lib.check(rc, what)
+
+    def dwt(self, stream=None) -> None:
+        self._call(self._fwd, self._px, self._pc, stream, "dwt")
 
     def idwt(self, stream=None) -> None:
         if self._py is None:
             raise ValueError("plan has no synthesis output")
-        with torch.cuda.device(self.device):
-            rc = self._inv(self._pc, self._py, self.levels, self._ws_ptr, self._ws_n,
-                           self._stream(stream))
-        if rc:
-            _lib.check(rc, "idwt")
+        self._call(self._inv, self._pc, self._py, stream, "idwt")
 
 
 class RaggedPlan:
@@ -283,9 +286,13 @@ class RaggedPlan:
         st = (torch.cuda.current_stream(self.device).cuda_stream if stream is None
               else getattr(stream, "cuda_stream", stream))
         # the persistent grid is sized from the current device's SM count
-        with torch.cuda.device(self.device):
+        if torch.cuda.current_device() == self.device.index:
             rc = fn(self._h, src.data_ptr(), haar_dtype(src.dtype), dst.data_ptr(),
                     haar_dtype(dst.dtype), self._ws.data_ptr(), self._ws_n, st)
+        else:
+            with torch.cuda.device(self.device):
+                rc = fn(self._h, src.data_ptr(), haar_dtype(src.dtype), dst.data_ptr(),
+                        haar_dtype(dst.dtype), self._ws.data_ptr(), self._ws_n, st)
         if rc:
             _lib.check(rc, "ragged transform")
         return dst

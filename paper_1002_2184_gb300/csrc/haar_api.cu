@@ -3,6 +3,8 @@
 // Host code only; every step of the transform itself runs in the kernels.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "fasthaar.h"
 #include "haar_internal.h"
 
@@ -214,6 +216,22 @@ int check_workspace(const Workspace& ws, void* workspace, size_t bytes) {
 }  // namespace
 
 namespace fh {
+// SM count of the current device, looked up once per device.
+int fast_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 1;
+  if (dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 // The argument checks of haar_dwt_2d alone, for the allocation-free variant
 // (haar_noalloc.cu), which must report argument errors before it looks at
 // the scratch size.

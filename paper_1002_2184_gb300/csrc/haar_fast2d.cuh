@@ -135,21 +135,18 @@ __device__ __forceinline__ void put_ll_epi(const Img2& im, int64_t row, int64_t 
 // Analysis of one 32 x 32 block by one warp: levels 1..min(L, 5), every
 // band stored; returns LL5 (used by a sixth level when L = 6).
 // ---------------------------------------------------------------------------
+// dwt_block32_regs takes the lane's 4 x 8 micro-block already loaded (rows
+// py .. py + 3, columns px .. px + 7 with py = y0 + 4 ty, px = x0 + 8 tx).
 template <typename Tin, typename Tout, int L, typename Epi = EpiStore>
-__device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, int64_t y0,
-                                                                int64_t x0, int lane,
-                                                                Epi&& epi = Epi()) {
+__device__ __forceinline__ typename AccT<Tin>::type dwt_block32_regs(
+    const Img2& im, int64_t y0, int64_t x0, int lane, typename AccT<Tin>::type (&v)[4][8],
+    Epi&& epi = Epi()) {
   using A = typename AccT<Tin>::type;
   static_assert(L >= 1 && L <= 6, "one warp fuses 1..6 levels");
   const int tx = lane & 3, ty = lane >> 2;
   const Bands<Tout> out{static_cast<Tout*>(im.dst), im.d_rs, im.h, im.w};
   const int64_t py = y0 + 4 * ty, px = x0 + 8 * tx;
   A l5 = A(0);
-
-  const Tin* src = static_cast<const Tin*>(im.src) + py * im.s_rs + px;
-  A v[4][8];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) load8(src + r * im.s_rs, v[r]);
 
   // ---- level 1: eight 2x2 blocks per lane ----
   A l1[2][4];
@@ -242,6 +239,19 @@ __device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, 
     }
   }
   return l5;
+}
+
+template <typename Tin, typename Tout, int L, typename Epi = EpiStore>
+__device__ __forceinline__ typename AccT<Tin>::type dwt_block32(const Img2& im, int64_t y0,
+                                                                int64_t x0, int lane,
+                                                                Epi&& epi = Epi()) {
+  using A = typename AccT<Tin>::type;
+  const int tx = lane & 3, ty = lane >> 2;
+  const Tin* src = static_cast<const Tin*>(im.src) + (y0 + 4 * ty) * im.s_rs + x0 + 8 * tx;
+  A v[4][8];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) load8(src + r * im.s_rs, v[r]);
+  return dwt_block32_regs<Tin, Tout, L>(im, y0, x0, lane, v, static_cast<Epi&&>(epi));
 }
 
 // Level 6 of one 64 x 64 block from the LL5 of its four 32 x 32 blocks.
@@ -374,36 +384,129 @@ __device__ __forceinline__ Img2 pass_image(const Pass& p, int64_t b, bool analys
 }
 
 // ---------------------------------------------------------------------------
-// Strided-batch kernels.  Analysis block of warps: 1 x 4 (32 x 128 px) for
-// L <= 5, 2 x 4 (64 x 128 px) for L = 6.  Synthesis: 1 x 4 for every L.
-// Four-warp blocks finish a launch with a finer tail than eight-warp ones
-// (4096^2 fp32, 5 levels: DWT + IDWT 41.45 against 42.12 us); two-warp
-// blocks measured the same as four.  The launch bounds below declare 256
-// threads, which fixes the register caps they state.
+// L2 warm-up before the dependency wait.  Every kernel starts with
+// griddepcontrol.wait, which holds it until the previous kernel in the stream
+// has finished; a block launched early (programmatic dependent launch) would
+// otherwise sit idle while the previous kernel drains, and the memory system
+// would restart from empty once the wait returns.  A block therefore first
+// asks L2 for the lines it is about to read (a prefetch is only a hint: the
+// loads after the wait still see every write of the previous kernel, since
+// L2 is the point of coherence), so the next launch's reads overlap the
+// previous launch's last writes.  One prefetch per whole 128-byte line:
+// several blocks or warps asking for parts of the same line measured slower
+// than no prefetch at all.
 // ---------------------------------------------------------------------------
-// Analysis: inputs of at most 2 bytes carry half the bytes per instruction
-// or less, so more resident warps hide more latency: registers capped for 6
-// blocks per SM (bf16 64 x 2048^2, 4 levels: 0.167 against 0.191 ms).  fp32
-// keeps its 5 blocks (42 registers; a cap for 6 measured slower); fp64, the
-// verification path, is not capped.
-template <typename Tin>
-constexpr int dwt_min_blocks() {
-  return sizeof(Tin) <= 2 ? 6 : sizeof(Tin) == 4 ? 5 : 1;
+__device__ __forceinline__ void l2_prefetch(const char* p, int bytes) {
+  if ((((uintptr_t)p | (unsigned)bytes) & 15u) == 0) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+  } else {
+    for (int o = 0; o < bytes; o += 128)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p + o) : "memory");
+  }
 }
-template <typename Tin, typename Tout, int L>
-__global__ void __launch_bounds__(256, dwt_min_blocks<Tin>()) k_dwt2d_fast(const Pass p) {
-  pdl_wait();
-  pdl_trigger();
+
+// One 128-byte piece of a band row: piece j of `row` of a band whose rows
+// start at base (pitch in bytes) and hold row_bytes bytes in this block.
+__device__ __forceinline__ void pf_piece(const char* base, int64_t pitch, int row, int j,
+                                         int64_t row_bytes) {
+  const int64_t off = (int64_t)j << 7;
+  const int64_t rest = row_bytes - off;
+  if (rest > 0) l2_prefetch(base + row * pitch + off, (int)(rest < 128 ? rest : 128));
+}
+
+// The analysis block's input: 32 * WR rows of 32 * WC samples, one 128-byte
+// piece per thread (the pieces are numbered row-major and dealt out over
+// the block's threads).
+template <typename Tin, int WR, int WC>
+__device__ __forceinline__ void dwt_prefetch(const Pass& p, int64_t b, int64_t by0,
+                                             int64_t bx0) {
+  constexpr int NL = (32 * WC * (int)sizeof(Tin) + 127) / 128;
+  const int64_t rows = p.h - by0 < 32 * WR ? p.h - by0 : 32 * WR;
+  const int64_t cols = p.w - bx0 < 32 * WC ? p.w - bx0 : 32 * WC;
+  const char* base = reinterpret_cast<const char*>(static_cast<const Tin*>(p.src) + b * p.s_bs +
+                                                   by0 * p.s_rs + bx0);
+  const int64_t pitch = p.s_rs * (int64_t)sizeof(Tin);
+  for (int s = threadIdx.x; s < rows * NL; s += blockDim.x)
+    pf_piece(base, pitch, s / NL, s % NL, cols * (int64_t)sizeof(Tin));
+}
+
+// The synthesis block's level-1 detail rows (16 rows of each band), level-2
+// rows (8 per band) and, for one or two levels, its low-band rows: deeper
+// levels are 1/16 of the data or less.  Pieces are dealt out one per thread
+// in the order level 1, level 2, low band.  (A version that built a table
+// of rectangles per block and looped over it measured 21.3 against 19.4 us
+// for this flat form, 4096^2 fp32, 5 levels.)
+template <typename Tin, typename A, int L, int WC>
+__device__ __forceinline__ void idwt_prefetch(const Pass& p, int64_t b, int64_t by0,
+                                              int64_t bx0) {
+  constexpr int ES = (int)sizeof(Tin);
+  constexpr int NL1 = (16 * WC * ES + 127) / 128, NL2 = (8 * WC * ES + 127) / 128;
+  constexpr int N1 = 3 * 16 * NL1, N2 = L >= 2 ? 3 * 8 * NL2 : 0;
+  constexpr int NLL = L == 1 ? 16 * NL1 : (L == 2 ? 8 * NL2 : 0);
+  const char* c = reinterpret_cast<const char*>(static_cast<const Tin*>(p.src) + b * p.s_bs);
+  const int64_t pitch = p.s_rs * ES;
+  const int64_t w1 = p.w >> 1, h1 = p.h >> 1, w2 = p.w >> 2, h2 = p.h >> 2;
+  const int64_t c1 = bx0 >> 1, r1 = by0 >> 1, c2 = bx0 >> 2, r2 = by0 >> 2;
+  const int64_t rb1 = (w1 - c1 < 16 * WC ? w1 - c1 : 16 * WC) * ES;
+  const int64_t rb2 = (w2 - c2 < 8 * WC ? w2 - c2 : 8 * WC) * ES;
+  for (int s = threadIdx.x; s < N1 + N2 + NLL; s += blockDim.x) {
+    if (s < N1) {
+      const int band = s / (16 * NL1), q = s - band * (16 * NL1);
+      const int64_t row = r1 + (band ? h1 : 0), col = c1 + (band != 1 ? w1 : 0);
+      pf_piece(c + (row * p.s_rs + col) * ES, pitch, q / NL1, q % NL1, rb1);
+    } else if (s < N1 + N2) {
+      const int t = s - N1, band = t / (8 * NL2), q = t - band * (8 * NL2);
+      const int64_t row = r2 + (band ? h2 : 0), col = c2 + (band != 1 ? w2 : 0);
+      pf_piece(c + (row * p.s_rs + col) * ES, pitch, q / NL2, q % NL2, rb2);
+    } else {
+      const int t = s - N1 - N2;
+      const int64_t lsz = p.ll_acc ? (int64_t)sizeof(A) : (int64_t)ES;
+      const char* ll = static_cast<const char*>(p.ll) + b * p.l_bs * lsz;
+      const int64_t lpitch = p.l_rs * lsz;
+      if constexpr (L == 1) {
+        const int64_t rb = rb1 / ES * lsz;
+        const int nl = (int)((rb + 127) >> 7);
+        if (t < 16 * nl) pf_piece(ll + (r1 * p.l_rs + c1) * lsz, lpitch, t / nl, t % nl, rb);
+      } else {
+        const int64_t rb = rb2 / ES * lsz;
+        const int nl = (int)((rb + 127) >> 7);
+        if (t < 8 * nl) pf_piece(ll + (r2 * p.l_rs + c2) * lsz, lpitch, t / nl, t % nl, rb);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strided-batch kernels.  A block is WC warps side by side (WC x 32 columns)
+// and, for the analysis with a sixth level, two such rows (64 rows, so the
+// four LL5 values of each 64 x 64 block meet in 32 bytes of shared memory).
+// WARPS is the number of resident warps per SM the register cap is set for
+// (0: no cap).  PF selects the L2 warm-up: 0 none, 1 every block, 2 the
+// blocks of the first wave only (p.pf_blocks), which are the ones that can
+// start while the previous kernel drains.
+// ---------------------------------------------------------------------------
+template <int WR, int WC, int WARPS>
+constexpr int fast_min_blocks() {
+  return WARPS == 0 ? 1 : (WARPS / (WR * WC) > 0 ? WARPS / (WR * WC) : 1);
+}
+
+template <typename Tin, typename Tout, int L, int WC, int WARPS, int PF>
+__global__ void __launch_bounds__(32 * WC * (L == 6 ? 2 : 1),
+                                  fast_min_blocks<(L == 6 ? 2 : 1), WC, WARPS>())
+    k_dwt2d_fast(const Pass p) {
   using A = typename AccT<Tin>::type;
   constexpr int WR = (L == 6) ? 2 : 1;
-  constexpr int WC = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t per = p.tiles_x * p.tiles_y;
   const int64_t t = blockIdx.x;
   const int64_t b = t / per, rr = t - b * per;
   const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
-  const int64_t y0 = cy * (32 * WR) + (warp / WC) * 32;
-  const int64_t x0 = cx * (32 * WC) + (warp % WC) * 32;
+  const int64_t by0 = cy * (32 * WR), bx0 = cx * (32 * WC);
+  if (PF == 1 || (PF == 2 && t < p.pf_blocks)) dwt_prefetch<Tin, WR, WC>(p, b, by0, bx0);
+  pdl_wait();
+  pdl_trigger();
+  const int64_t y0 = by0 + (warp / WC) * 32;
+  const int64_t x0 = bx0 + (warp % WC) * 32;
   const Img2 im = pass_image<Tin, Tout>(p, b, true);
   A l5 = A(0);
   if (y0 < p.h && x0 < p.w) l5 = dwt_block32<Tin, Tout, L>(im, y0, x0, lane);
@@ -413,76 +516,133 @@ __global__ void __launch_bounds__(256, dwt_min_blocks<Tin>()) k_dwt2d_fast(const
     __syncthreads();
     if (threadIdx.x < WC / 2) {
       const int j = threadIdx.x;
-      const int64_t by0 = cy * 64, bx0 = cx * 128 + 64 * j;
-      if (by0 < p.h && bx0 < p.w)
-        dwt_level6<Tout>(im, s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j], s5[1][2 * j + 1],
-                         by0, bx0);
+      const int64_t y6 = by0, x6 = bx0 + 64 * j;
+      if (y6 < p.h && x6 < p.w)
+        dwt_level6<Tout>(im, s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j], s5[1][2 * j + 1], y6,
+                         x6);
     }
   }
 }
 
-// Synthesis with FP32 arithmetic: registers capped for 6 resident blocks per
-// SM (40 registers; measured 2 % faster than 5 blocks at 42 registers on the
-// 4096^2 fp32 case).  FP64 arithmetic needs twice the registers: no cap.
-template <typename Tin>
-constexpr int idwt_min_blocks() {
-  return sizeof(typename AccT<Tin>::type) == 8 ? 1 : 6;
-}
-template <typename Tin, typename Tout, int L>
-__global__ void __launch_bounds__(256, idwt_min_blocks<Tin>()) k_idwt2d_fast(const Pass p) {
-  pdl_wait();
-  pdl_trigger();
+template <typename Tin, typename Tout, int L, int WC, int WARPS, int PF>
+__global__ void __launch_bounds__(32 * WC, fast_min_blocks<1, WC, WARPS>())
+    k_idwt2d_fast(const Pass p) {
+  using A = typename AccT<Tin>::type;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t per = p.tiles_x * p.tiles_y;
   const int64_t t = blockIdx.x;
   const int64_t b = t / per, rr = t - b * per;
   const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
-  const int64_t y0 = cy * 32, x0 = cx * 128 + warp * 32;
+  const int64_t by0 = cy * 32, bx0 = cx * (32 * WC);
+  if (PF == 1 || (PF == 2 && t < p.pf_blocks)) idwt_prefetch<Tin, A, L, WC>(p, b, by0, bx0);
+  pdl_wait();
+  pdl_trigger();
+  const int64_t y0 = by0, x0 = bx0 + warp * 32;
   if (y0 >= p.h || x0 >= p.w) return;
   idwt_block32<Tin, Tout, L>(pass_image<Tin, Tout>(p, b, false), y0, x0, lane);
 }
 
-template <typename Tin, typename Tout>
-cudaError_t dwt2d_fast_t(Pass p, cudaStream_t s) {
-  const int CH = p.levels == 6 ? 64 : 32, CW = 128;
+// SM count of the current device (cached per device).
+int fast_sm_count();
+
+// Launchers for one configuration; the blocks of the first wave are the
+// SM count times the resident blocks per SM the register cap allows.
+template <typename Tin, typename Tout, int WC, int WARPS, int PF>
+cudaError_t dwt2d_fast_cfg(Pass p, cudaStream_t s) {
+  const int CH = p.levels == 6 ? 64 : 32, CW = 32 * WC;
   p.tiles_x = (p.w + CW - 1) / CW;
   p.tiles_y = (p.h + CH - 1) / CH;
   p.ntiles = p.batch * p.tiles_x * p.tiles_y;
   if (p.ntiles == 0) return cudaSuccess;
   if (p.ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int wr = p.levels == 6 ? 2 : 1;
+  p.pf_blocks = (int64_t)fast_sm_count() * (WARPS ? WARPS / (wr * WC) : 1);
   const unsigned g = (unsigned)p.ntiles;
   cudaError_t e = cudaSuccess;
   switch (p.levels) {
-    case 1: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 1>, g, 128, s, p); break;
-    case 2: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 2>, g, 128, s, p); break;
-    case 3: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 3>, g, 128, s, p); break;
-    case 4: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 4>, g, 128, s, p); break;
-    case 5: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 5>, g, 128, s, p); break;
-    case 6: e = launch_pdl(k_dwt2d_fast<Tin, Tout, 6>, g, 256, s, p); break;
+#define FH_DWT_CASE(LV)                                                                       \
+  case LV:                                                                                    \
+    e = launch_pdl(k_dwt2d_fast<Tin, Tout, LV, WC, WARPS, PF>, g, 32 * WC * (LV == 6 ? 2 : 1), \
+                   s, p);                                                                     \
+    break;
+    FH_DWT_CASE(1)
+    FH_DWT_CASE(2)
+    FH_DWT_CASE(3)
+    FH_DWT_CASE(4)
+    FH_DWT_CASE(5)
+    FH_DWT_CASE(6)
+#undef FH_DWT_CASE
     default: return cudaErrorInvalidValue;
   }
   return e;
 }
 
-template <typename Tin, typename Tout>
-cudaError_t idwt2d_fast_t(Pass p, cudaStream_t s) {
-  p.tiles_x = (p.w + 127) / 128;
+template <typename Tin, typename Tout, int WC, int WARPS, int PF>
+cudaError_t idwt2d_fast_cfg(Pass p, cudaStream_t s) {
+  const int CW = 32 * WC;
+  p.tiles_x = (p.w + CW - 1) / CW;
   p.tiles_y = (p.h + 31) / 32;
   p.ntiles = p.batch * p.tiles_x * p.tiles_y;
   if (p.ntiles == 0) return cudaSuccess;
   if (p.ntiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  p.pf_blocks = (int64_t)fast_sm_count() * (WARPS ? WARPS / WC : 1);
   const unsigned g = (unsigned)p.ntiles;
+  const unsigned nt = 32 * WC;
   cudaError_t e = cudaSuccess;
   switch (p.levels) {
-    case 1: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 1>, g, 128, s, p); break;
-    case 2: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 2>, g, 128, s, p); break;
-    case 3: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 3>, g, 128, s, p); break;
-    case 4: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 4>, g, 128, s, p); break;
-    case 5: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 5>, g, 128, s, p); break;
-    case 6: e = launch_pdl(k_idwt2d_fast<Tin, Tout, 6>, g, 128, s, p); break;
+#define FH_IDWT_CASE(LV)                                                          \
+  case LV:                                                                        \
+    e = launch_pdl(k_idwt2d_fast<Tin, Tout, LV, WC, WARPS, PF>, g, nt, s, p);     \
+    break;
+    FH_IDWT_CASE(1)
+    FH_IDWT_CASE(2)
+    FH_IDWT_CASE(3)
+    FH_IDWT_CASE(4)
+    FH_IDWT_CASE(5)
+    FH_IDWT_CASE(6)
+#undef FH_IDWT_CASE
     default: return cudaErrorInvalidValue;
   }
   return e;
+}
+
+// The configuration used per storage type, measured on 4096^2 fp32 with 5
+// levels (one image per launch, where the warm-up matters most) and on the
+// 64 x 2048^2 batch with 4 levels (fraction of the measured copy bandwidth):
+//  * fp32 analysis: 2-warp blocks, 32 resident warps (64 registers; 24 and
+//    48 warps were 1-2 % slower), warm-up in every block: 4096^2 19.5 us
+//    (101 %) against 21.7 us without; batch 106 % against 105 %;
+//  * fp32 synthesis: 2-warp blocks, 40 warps (48 registers), every block:
+//    4096^2 19.4 against 21.6 us; batch 106 % against 105 %;
+//  * 16-bit storage: 48 warps, warm-up in the first wave only (in every
+//    block it costs more issue than it saves when a block moves half the
+//    bytes: bf16 analysis 88 %, synthesis 86 %; first wave only 95 % and
+//    101 %, none 95 % and 101 %); a synthesis writing fp32 keeps it in every
+//    block (104 % against 103 %);
+//  * uint8 input: 4-warp blocks (a block row is one 128-byte line), 48
+//    warps, first wave only (79 %: bound by instruction issue at 3 bytes per
+//    pixel, not by the warm-up);
+//  * FP64 (the verification path): no register cap.
+template <typename Tin> struct DwtCfg {
+  static constexpr int WC = sizeof(Tin) == 1 ? 4 : 2;
+  static constexpr int WARPS = sizeof(Tin) == 8 ? 0 : (sizeof(Tin) == 4 ? 32 : 48);
+  static constexpr int PF = sizeof(Tin) >= 4 ? 1 : 2;
+};
+template <typename Tin, typename Tout> struct IdwtCfg {
+  static constexpr int WC = sizeof(Tin) == 2 ? 4 : 2;
+  static constexpr int WARPS = sizeof(Tin) == 8 ? 0 : (sizeof(Tin) == 4 ? 40 : 48);
+  static constexpr int PF = (sizeof(Tin) >= 4 || sizeof(Tout) >= 4) ? 1 : 2;
+};
+
+template <typename Tin, typename Tout>
+cudaError_t dwt2d_fast_t(Pass p, cudaStream_t s) {
+  using C = DwtCfg<Tin>;
+  return dwt2d_fast_cfg<Tin, Tout, C::WC, C::WARPS, C::PF>(p, s);
+}
+template <typename Tin, typename Tout>
+cudaError_t idwt2d_fast_t(Pass p, cudaStream_t s) {
+  using C = IdwtCfg<Tin, Tout>;
+  return idwt2d_fast_cfg<Tin, Tout, C::WC, C::WARPS, C::PF>(p, s);
 }
 
 }  // namespace fh

@@ -42,6 +42,7 @@ struct Pass {
   int64_t batch, h, w;
   // filled in by the launcher
   int64_t tiles_x, tiles_y, ntiles;
+  int64_t pf_blocks;  // blocks that warm L2 before their dependency wait
 };
 
 // Tile shapes of the generic 2D kernels (vector path); the scalar path always

@@ -83,8 +83,12 @@ __device__ __forceinline__ Img2 ragged_image(const RaggedArgs& a, const RaggedIm
 // Both ragged kernels: FP32 arithmetic capped at 40 registers for 6 resident
 // blocks per SM (the 512-image batch: analysis 0.706 against 0.783 ms,
 // synthesis 0.711 against 0.741 ms); FP64 is not capped.
+template <typename Tin>
+constexpr int ragged_min_blocks() {
+  return sizeof(typename AccT<Tin>::type) == 8 ? 1 : 6;
+}
 template <typename Tin, typename Tout, int UH, int UW>
-__global__ void __launch_bounds__(256, idwt_min_blocks<Tin>()) k_ragged_dwt2d(const RaggedArgs a) {
+__global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_dwt2d(const RaggedArgs a) {
   pdl_wait();
   pdl_trigger();
   using A = typename AccT<Tin>::type;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(256, idwt_min_blocks<Tin>()) k_ragged_dwt2d(co
 }
 
 template <typename Tin, typename Tout, int UH, int UW>
-__global__ void __launch_bounds__(256, idwt_min_blocks<Tin>()) k_ragged_idwt2d(const RaggedArgs a) {
+__global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_idwt2d(const RaggedArgs a) {
   pdl_wait();
   pdl_trigger();
   constexpr int WC = UW / 32;

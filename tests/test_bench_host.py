@@ -21,3 +21,15 @@ def test_lattice_taps_with_one_angle_is_a_rotation():
     # one stage: h = (cos a, sin a); a = pi/4 gives the Haar low-pass
     h = bench.lattice_taps([np.pi / 4])
     assert np.allclose(h, [2 ** -0.5, 2 ** -0.5], atol=1e-15)
+
+
+def test_kernel_hash_ignores_comments_and_layout():
+    """The recorded DRAM traffic is keyed to the kernel code: comment or
+    whitespace edits keep the key, a change of code changes it."""
+    a = "int f(int x) {\n  return x + 1;  // add one\n}\n/* trailing */"
+    b = "/* header */ int f(int x) { return x + 1; }"
+    c = "int f(int x) { return x + 2; }"
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
+    s = 'asm("cp.async.bulk [%0]; // not a comment");'
+    assert "// not a comment" in bench.code_only(s)
