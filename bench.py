@@ -13,8 +13,8 @@ step, so every rank runs an independent replica and the value is the sum of
 all ranks' samples over the slowest rank's time ("weak" scaling).
 
 ``--impl reference`` times the FP64 CPU oracle (the plain definition of the
-filter bank) on the host cores instead, on a bounded crop of the same image
-per step; it runs on rank 0 only.
+filter bank) on the host instead, one full round trip of the same image per
+step; it runs on rank 0 only.
 """
 from __future__ import annotations
 
@@ -339,6 +339,7 @@ def run_ours(args):
     # correctness guard on the timed data: the round trip reproduces the input
     err = float(torch.linalg.vector_norm((ys[0] - xs[0]).double()) /
                 torch.linalg.vector_norm(xs[0].double()))
+    head = (host64(xs[0]), host64(cs[0]), host64(ys[0]))  # checked against the oracle
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
@@ -397,10 +398,10 @@ def run_ours(args):
 
     if not args.no_e2e:
         out["e2e"] = e2e_ours(api, synth, dev, cfg, max(10, min(args.steps, 50)), world)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_oracle(synth, cfg)
     if not args.no_forms:
         out["forms"] = forms(api, synth, dev, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["accuracy"] = cpu_leg(synth, cfg, head, out.get("forms"))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -488,30 +489,141 @@ def e2e_ours(api, synth, dev, cfg, steps, world):
                       "without the transforms"}
 
 
-def cpu_baseline_oracle(synth, cfg, min_seconds=10.0):
-    """The FP64 oracle as it stands, single-threaded, on this host: DWT + IDWT
-    of the full 4096 x 4096 image, repeated for about ``min_seconds``."""
+def cpu_leg(synth, cfg, head, forms_out, min_seconds=6.0):
+    """The host-side leg of the benchmark (rank 0, one GPU only): the FP64
+    oracle as it stands timed on this host's cores, the FP32 CPU baseline
+    (the same method as a plain loop, one core), and the accuracy of every
+    sampled GPU result against the oracle.
+
+    head: host copies (x, coef, recon) of the headline image as the GPU
+    produced them.  forms_out: the forms dict, whose entries get their
+    "accuracy" here.  Returns (cpu_baseline dict, headline accuracy dict)."""
+    import concurrent.futures as cf
     import oracle
+    from oracle import cpu_baseline as fp32cpu
     H, W, L = cfg.h, cfg.w, cfg.levels
     x = synth.piecewise_smooth_image(H, W, cfg.seed, 0).astype(np.float32).astype(np.float64)
     oracle.lib()
+
+    # (a) the oracle, one thread, the full headline image
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.idwt2d(oracle.dwt2d(x, L), L)
+        c_ref = oracle.dwt2d(x, L)
+        oracle.idwt2d(c_ref, L)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
             break
-    return {"value": round(H * W * reps / el / 1e9, 5), "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": f"{reps} round trips of the full {H}x{W} image, {L} levels, "
-                      f"FP64 C oracle, one thread ({el:.1f} s)"}
+    out = {"value": round(H * W * reps / el / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{reps} round trips of the full {H}x{W} image, {L} levels, FP64 C oracle, "
+                     f"one thread ({el:.1f} s)"}
+    head_acc = {"vs": "FP64 oracle", "sample": f"the {H}x{W} image of input set 0",
+                "coef": err_stats([(head[1], c_ref)]),
+                "recon": err_stats([(head[2], oracle.idwt2d(c_ref, L))])}
+
+    # (b) the same method as a plain FP32 loop, one core, -O3
+    xf = x.astype(np.float32)
+    fp32cpu.dwt2d_f32(xf, L)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fp32cpu.idwt2d_f32(fp32cpu.dwt2d_f32(xf, L), L)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= 2.0:
+            break
+    out["fp32_fast_haar_one_core"] = {
+        "value": round(H * W * reps / el / 1e9, 4), "unit": UNIT, "cores": 1,
+        "kind": "the Fast Haar butterfly as a plain FP32 loop (gcc -O3, no SIMD intrinsics)",
+        "sample": f"{reps} round trips of the {H}x{W} image ({el:.1f} s)"}
+
+    # (c) the oracle on every host core, one image per thread, on the
+    # precision, ragged and differentiation workloads (bounded samples)
+    cores = os.cpu_count() or 1
+    multi = {"cores": cores, "kind": "oracle, one image per thread"}
+    with cf.ThreadPoolExecutor(max_workers=cores) as pool:
+        def timed(jobs, px, seconds=2.0):
+            # whole rounds of the job list until `seconds` have passed
+            rounds, t = 0, time.perf_counter()
+            while True:
+                list(pool.map(lambda f: f(), jobs))
+                rounds += 1
+                el = time.perf_counter() - t
+                if el >= seconds:
+                    return round(rounds * px / el / 1e9, 5), round(el, 2)
+
+        pcfg = synth.PrecisionBatch()
+        imgs = [synth.piecewise_smooth_image(pcfg.h, pcfg.w, pcfg.seed, i) for i in range(cores)]
+        v, el = timed([lambda a=a: oracle.idwt2d(oracle.dwt2d(a, pcfg.levels), pcfg.levels)
+                       for a in imgs], cores * pcfg.h * pcfg.w)
+        multi["precision"] = {"value": v, "unit": UNIT, "seconds": el,
+                              "sample": f"rounds of {cores} images of {pcfg.h}x{pcfg.w}, "
+                                        f"{pcfg.levels} levels, DWT + IDWT"}
+        rcfg = synth.RaggedBatch()
+        items = synth.ragged_shapes(rcfg)[:2 * cores]
+        rim = [synth.piecewise_smooth_image(h, w, rcfg.seed, i) for i, (h, w, _) in
+               enumerate(items)]
+        v, el = timed([lambda a=a, lv=lv: oracle.idwt2d(oracle.dwt2d(a, lv), lv)
+                       for a, (_, _, lv) in zip(rim, items)], sum(h * w for h, w, _ in items))
+        multi["ragged"] = {"value": v, "unit": UNIT, "seconds": el,
+                           "sample": f"rounds of the first {len(items)} images of the ragged "
+                                     "batch, DWT + IDWT"}
+        gcfg = synth.GradBatch()
+        _, C, gh, gw = gcfg.shape
+        gim = [synth.piecewise_smooth_image(gh, gw, gcfg.seed, i)[None, None] for i in
+               range(cores)]
+        v, el = timed([lambda a=a: (oracle.denoise_loss(a, gcfg.levels, gcfg.threshold,
+                                                        gcfg.l1_weight),
+                                    oracle.denoise_loss_grad(a, gcfg.levels, gcfg.threshold,
+                                                             gcfg.l1_weight))
+                       for a in gim], cores * gh * gw)
+        multi["backward"] = {"value": v, "unit": UNIT, "seconds": el,
+                             "sample": f"rounds of {cores} channels of {gh}x{gw}, loss and "
+                                       "gradient"}
+    out["multi_core"] = multi
+
+    # (d) accuracy of every sampled result
+    for form, entry, check in ACCURACY:
+        res = check(oracle)
+        tgt = forms_out.get(form) if forms_out else None
+        if tgt is None:
+            continue
+        (tgt[entry] if entry else tgt)["accuracy"] = res
+    return out, head_acc
 
 
 # ---------------------------------------------------------------------------
 # secondary forms, each next to the plain fp32 path on the same GPU
 # ---------------------------------------------------------------------------
-def time_ms(fn, iters, warmup=3):
+# Accuracy of each result against the FP64 oracle.  The GPU side only copies
+# its outputs for a few sampled items to host memory here; the oracle runs in
+# the CPU-baseline leg (cpu_leg), which fills in each form's "accuracy".
+ACCURACY = []  # (form name, entry name or None, function(oracle) -> dict)
+
+
+def err_stats(pairs):
+    """max-abs and relative L2 over (result, reference) pairs of float64
+    arrays; rel-L2 is over all pairs together."""
+    num = den = mx = scale = 0.0
+    for got, ref in pairs:
+        d = got - ref
+        num += float(np.sum(d * d))
+        den += float(np.sum(ref * ref))
+        mx = max(mx, float(np.max(np.abs(d))) if d.size else 0.0)
+        scale = max(scale, float(np.max(np.abs(ref))) if ref.size else 0.0)
+    return {"max_abs": mx, "rel_l2": (num / den) ** 0.5 if den > 0 else num ** 0.5,
+            "max_abs_over_max_ref": mx / scale if scale > 0 else mx}
+
+
+def host64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def time_med(fn, reps=50, warmup=3, min_group_ms=0.25):
+    """Per-call device time: the median over ``reps`` groups of back-to-back
+    calls, CUDA events on the current stream between the groups (no gap and
+    no synchronisation between them).  A group holds enough calls to last
+    about ``min_group_ms``, so short calls are not dominated by the event."""
+    import math
     import torch
     for _ in range(warmup):
         fn()
@@ -519,11 +631,20 @@ def time_ms(fn, iters, warmup=3):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record()
-    for _ in range(iters):
+    for _ in range(3):
         fn()
     b.record()
     torch.cuda.synchronize()
-    return a.elapsed_time(b) / iters
+    one = max(a.elapsed_time(b) / 3, 1e-4)
+    g = max(1, int(math.ceil(min_group_ms / one)))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record()
+    for r in range(reps):
+        for _ in range(g):
+            fn()
+        ev[r + 1].record()
+    torch.cuda.synchronize()
+    return statistics.median(ev[r].elapsed_time(ev[r + 1]) / g for r in range(reps))
 
 
 def forms(api, synth, dev, world):
@@ -544,8 +665,16 @@ def forms(api, synth, dev, world):
         p1.dwt()
         p1.idwt()
 
-    ms_eager = time_ms(lambda: (p1.dwt(), p1.idwt()), 200)
-    ms = time_ms(g1.replay, 200)
+    ms_eager = time_med(lambda: (p1.dwt(), p1.idwt()))
+    ms = time_med(g1.replay)
+    s1 = (host64(x1), host64(c1), host64(y1))
+
+    def check_signal(orc, s1=s1, L=sc.levels):
+        ref = orc.dwt1d(s1[0], L)
+        return {"vs": "FP64 oracle", "sample": "the whole signal",
+                "coef": err_stats([(s1[1], ref)]),
+                "recon": err_stats([(s1[2], orc.idwt1d(ref, L))])}
+    ACCURACY.append(("signal_1d", None, check_signal))
     res["signal_1d"] = {"workload": f"1D fp32 signal n={sc.n}, {sc.levels} level, DWT+IDWT",
                         "us_per_round_trip": round(ms * 1e3, 2),
                         "us_per_round_trip_eager": round(ms_eager * 1e3, 2),
@@ -585,16 +714,29 @@ def forms(api, synth, dev, world):
             plan.dwt()
             plan.idwt()
 
-        ms = time_ms(rt, 5, warmup=2)
+        ms = time_med(rt)
         nbytes = px * (x.element_size() + 2 * c.element_size() + y.element_size())
-        dwt_ms = time_ms(plan.dwt, 5, warmup=2)
-        idwt_ms = time_ms(plan.idwt, 5, warmup=2)
+        dwt_ms = time_med(plan.dwt)
+        idwt_ms = time_med(plan.idwt)
         entry[name] = {"ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
                        "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                        "dwt_gbs": round(px * (x.element_size() + c.element_size())
                                         / (dwt_ms * 1e-3) / 1e9, 1),
                        "idwt_gbs": round(px * (c.element_size() + y.element_size())
                                          / (idwt_ms * 1e-3) / 1e9, 1)}
+        # three images spread over the batch: the stored input (exactly what
+        # the GPU read), its stored coefficients and reconstruction
+        picks = (0, pc.batch * 37 // 64, pc.batch - 1)
+        smp = [(host64(x[i]), host64(c[i]), host64(y[i])) for i in picks]
+
+        def check(orc, smp=smp, L=pc.levels, picks=picks):
+            refs = [orc.dwt2d(xi, L) for xi, _, _ in smp]
+            rec = [orc.idwt2d(r, L) for r in refs]
+            return {"vs": "FP64 oracle on the stored input values",
+                    "sample": f"images {list(picks)} of the batch",
+                    "coef": err_stats([(ci, r) for (_, ci, _), r in zip(smp, refs)]),
+                    "recon": err_stats([(yi, r) for (_, _, yi), r in zip(smp, rec)])}
+        ACCURACY.append(("precision", name, check))
         del x, c, y, plan
     for name in ("bf16", "fp16", "u8_in_bf16_coef_fp32_out"):
         entry[name]["speedup_vs_fp32"] = round(entry["fp32"]["ms"] / entry[name]["ms"], 3)
@@ -647,7 +789,7 @@ def grad_form(api, synth, dev):
             pl.backward(stream=st)
         for st in side:
             cap.wait_stream(st)
-    ms_graph = time_ms(g.replay, 20) / sets
+    ms_graph = time_med(g.replay) / sets
 
     xr = x.clone().requires_grad_(True)
 
@@ -659,12 +801,26 @@ def grad_form(api, synth, dev):
         xr.grad = None
         ad.denoise_loss_unfused(xr, L, t, lam).backward()
 
-    ms_fused = time_ms(fused_eager, 20)
-    ms_unfused = time_ms(unfused_eager, 20)
+    ms_fused = time_med(fused_eager)
+    ms_unfused = time_med(unfused_eager)
+    # loss and gradient of the whole batch from the fused kernels
+    pl0 = plans[0]
+    loss_gpu = float(pl0.forward().item())
+    grad_gpu = host64(pl0.backward())
+    x_host = host64(x)
+
+    def check_grad(orc, x_host=x_host, loss_gpu=loss_gpu, grad_gpu=grad_gpu):
+        loss_ref = orc.denoise_loss(x_host, L, t, lam)[0]
+        g_ref = orc.denoise_loss_grad(x_host, L, t, lam)
+        return {"vs": "FP64 oracle (closed-form gradient)", "sample": "the whole batch",
+                "loss_gpu": loss_gpu, "loss_oracle": loss_ref,
+                "loss_rel_err": abs(loss_gpu - loss_ref) / abs(loss_ref),
+                "grad": err_stats([(grad_gpu, g_ref)])}
+    ACCURACY.append(("backward", None, check_grad))
     c = torch.empty_like(x)
     y = torch.empty_like(x)
     rt = api.Plan(x, c, L, y)
-    ms_rt = time_ms(lambda: (rt.dwt(), rt.idwt()), 50)
+    ms_rt = time_med(lambda: (rt.dwt(), rt.idwt()))
     peaks = measured_peaks()
     hbm = (peaks or {}).get("hbm_gbs") or 6800.0
     gbs = 12.0 * px / (ms_graph * 1e-3) / 1e9
@@ -697,15 +853,15 @@ def signal_batch_form(api, synth, dev):
     c = torch.empty_like(x)
     y = torch.empty_like(x)
     plan = api.Plan(x, c, L, y, one_d=True)
-    ms_rt = time_ms(lambda: (plan.dwt(), plan.idwt()), 20)
-    ms_dn = time_ms(lambda: api.denoise1d(x, L, 1.0, out=y), 20)
+    ms_rt = time_med(lambda: (plan.dwt(), plan.idwt()))
+    ms_dn = time_med(lambda: api.denoise1d(x, L, 1.0, out=y))
     # the paper's comparison, existing vs fast, at scale: one level of the
     # undecimated direct form (every convolution output computed, 12 B per
     # sample) against the Fast Haar analysis (the decimated outputs only)
     u = torch.empty((rows, 2, n), dtype=x.dtype, device=dev)
     p1 = api.Plan(x, c, 1, y, one_d=True)
-    ms_direct = time_ms(lambda: api.swt1d(x, 1, out=u), 20)
-    ms_fast = time_ms(p1.dwt, 20)
+    ms_direct = time_med(lambda: api.swt1d(x, 1, out=u))
+    ms_fast = time_med(p1.dwt)
     same = bool(torch.equal(u[:, 1, ::2], c[:, n // 2:]))
     px = rows * n
     hbm = _hbm()
@@ -753,11 +909,11 @@ def filter_form(api, synth, dev):
     out = {"workload": f"{rows} x 2^20 fp32 signals, {L} levels, DWT + IDWT, periodic"}
     for name, taps in (("haar_k2", api.HAAR2), ("daubechies4_k4", api.DAUBECHIES4),
                        ("lattice_k8", lattice_taps([0.2, 0.5, -0.4, 0.9]))):
-        ms = time_ms(lambda: (api.filter_dwt1d(x, L, taps, out=c),
-                              api.filter_idwt1d(c, L, taps, out=y)), 20)
+        ms = time_med(lambda: (api.filter_dwt1d(x, L, taps, out=c),
+                               api.filter_idwt1d(c, L, taps, out=y)))
         ok = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)) <= 1e-6
-        dwt_ms = time_ms(lambda: api.filter_dwt1d(x, L, taps, out=c), 20)
-        idwt_ms = time_ms(lambda: api.filter_idwt1d(c, L, taps, out=y), 20)
+        dwt_ms = time_med(lambda: api.filter_dwt1d(x, L, taps, out=c))
+        idwt_ms = time_med(lambda: api.filter_idwt1d(c, L, taps, out=y))
         out[name] = {"ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
                      "frac_of_hbm": round(16.0 * px / (ms * 1e-3) / 1e9 / _hbm(), 4),
                      "dwt_frac_of_hbm": round(8.0 * px / (dwt_ms * 1e-3) / 1e9 / _hbm(), 4),
@@ -768,8 +924,8 @@ def filter_form(api, synth, dev):
     xs = x.reshape(-1, 4096)
     cs, ys = c.reshape(-1, 4096), y.reshape(-1, 4096)
     taps = api.DAUBECHIES4
-    dwt_ms = time_ms(lambda: api.filter_dwt1d(xs, L, taps, out=cs), 20)
-    idwt_ms = time_ms(lambda: api.filter_idwt1d(cs, L, taps, out=ys), 20)
+    dwt_ms = time_med(lambda: api.filter_dwt1d(xs, L, taps, out=cs))
+    idwt_ms = time_med(lambda: api.filter_idwt1d(cs, L, taps, out=ys))
     ok = float(torch.linalg.vector_norm(ys - xs) / torch.linalg.vector_norm(xs)) <= 1e-6
     out["daubechies4_k4_16384x4096"] = {
         "dwt_frac_of_hbm": round(8.0 * px / (dwt_ms * 1e-3) / 1e9 / _hbm(), 4),
@@ -788,7 +944,7 @@ def volume_form(api, synth, dev):
     x = torch.stack([sl[i % 8] for i in range(side)]).to(dev)
     c = torch.empty_like(x)
     y = torch.empty_like(x)
-    ms = time_ms(lambda: (api.dwt3d(x, L, out=c), api.idwt3d(c, L, out=y)), 20)
+    ms = time_med(lambda: (api.dwt3d(x, L, out=c), api.idwt3d(c, L, out=y)))
     ok = float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)) <= 1e-6
     px = x.numel()
     return {"workload": f"{side}^3 fp32 volume, {L} levels, DWT + IDWT",
@@ -807,8 +963,8 @@ def denoise2d_form(api, synth, dev):
     y = torch.empty_like(x)
     c = torch.empty_like(x)
     plan = api.Plan(x, c, cfg.levels, y)
-    ms_rt = time_ms(lambda: (plan.dwt(), plan.idwt()), 20)
-    ms_dn = time_ms(lambda: api.denoise2d(x, cfg.levels, 0.05, out=y), 20)
+    ms_rt = time_med(lambda: (plan.dwt(), plan.idwt()))
+    ms_dn = time_med(lambda: api.denoise2d(x, cfg.levels, 0.05, out=y))
     px = x.numel()
     hbm = _hbm()
     return {"workload": f"4 x {cfg.h}x{cfg.w} fp32 images, {cfg.levels} levels, soft t=0.05",
@@ -848,9 +1004,21 @@ def ragged_form(api, synth, dev, dense_fp32_gsamples):
     with torch.cuda.graph(g):
         plan.dwt(x, c)
         plan.idwt(c, y)
-    ms = time_ms(g.replay, 20)
+    ms = time_med(g.replay)
     ok = plan.status() == 0
     err = float(torch.linalg.vector_norm((y - x).double()) / torch.linalg.vector_norm(x.double()))
+    picks = sorted(np.random.default_rng(2184).choice(len(items), size=6, replace=False).tolist())
+    xv_, cv_, yv_ = plan.views(x), plan.views(c), plan.views(y)
+    smp = [(host64(xv_[i]), host64(cv_[i]), host64(yv_[i]), items[i][2]) for i in picks]
+
+    def check_ragged(orc, smp=smp, picks=picks):
+        refs = [orc.dwt2d(xi, L) for xi, _, _, L in smp]
+        rec = [orc.idwt2d(r, L) for r, (_, _, _, L) in zip(refs, smp)]
+        return {"vs": "FP64 oracle", "sample": f"images {picks} "
+                f"({', '.join(f'{a.shape[0]}x{a.shape[1]} L{L}' for a, _, _, L in smp)})",
+                "coef": err_stats([(ci, r) for (_, ci, _, _), r in zip(smp, refs)]),
+                "recon": err_stats([(yi, r) for (_, _, yi, _), r in zip(smp, rec)])}
+    ACCURACY.append(("ragged", None, check_ragged))
     # the plain path: one strided-batch plan per image, launched one by one
     per = [api.Plan(xv, cv, items[i][2], yv) for i, (xv, cv, yv) in
            enumerate(zip(plan.views(x), plan.views(c), plan.views(y)))]
@@ -860,7 +1028,7 @@ def ragged_form(api, synth, dev, dense_fp32_gsamples):
             p_.dwt()
             p_.idwt()
 
-    ms_loop = time_ms(loop, 3, warmup=1)
+    ms_loop = time_med(loop, warmup=1)
     peaks = measured_peaks()
     hbm = (peaks or {}).get("hbm_gbs") or 6800.0
     gbs = 16.0 * px / (ms * 1e-3) / 1e9
@@ -940,20 +1108,17 @@ def run_reference(args):
     cfg = synth.Image2D()
     H, W, L = cfg.h, cfg.w, cfg.levels
     img = synth.piecewise_smooth_image(H, W, cfg.seed, 0).astype(np.float32).astype(np.float64)
-    # each step: DWT + IDWT of one 1024 x 1024 crop (a bounded sample)
-    side = 1024
-    crops = [img[i * side:(i + 1) * side, j * side:(j + 1) * side]
-             for i in range(H // side) for j in range(W // side)]
+    # each step: DWT + IDWT of the full image, as the GPU arm's step
     oracle.lib()
     for k in range(args.warmup):
-        oracle.idwt2d(oracle.dwt2d(crops[k % len(crops)], L), L)
+        oracle.idwt2d(oracle.dwt2d(img, L), L)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.idwt2d(oracle.dwt2d(crops[k % len(crops)], L), L)
+        oracle.idwt2d(oracle.dwt2d(img, L), L)
     el = time.perf_counter() - t0
-    value = side * side * args.steps / el / 1e9
-    sample = (f"each step: DWT+IDWT of one {side}x{side} crop of the {H}x{W} image, "
-              f"{L} levels, FP64 C oracle, one thread")
+    value = H * W * args.steps / el / 1e9
+    sample = (f"each step: DWT+IDWT of the full {H}x{W} image, {L} levels, FP64 C oracle, "
+              "one thread")
     out = {
         "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
