@@ -790,6 +790,21 @@ def grad_form(api, synth, dev):
         for st in side:
             cap.wait_stream(st)
     ms_graph = time_med(g.replay) / sets
+    # each direction alone, back to back on the rotating sets: the forward
+    # (loss kernel + the one-thread finalize) reads x, 4 B per pixel; the
+    # backward reads x and writes the gradient, 8 B per pixel
+    turn = [0]
+
+    def fwd_only():
+        plans[turn[0] % sets].forward()
+        turn[0] += 1
+
+    def bwd_only():
+        plans[turn[0] % sets].backward()
+        turn[0] += 1
+
+    ms_fwd = time_med(fwd_only)
+    ms_bwd = time_med(bwd_only)
 
     xr = x.clone().requires_grad_(True)
 
@@ -831,6 +846,10 @@ def grad_form(api, synth, dev):
             "fused_graph_gsamples_s": round(px / (ms_graph * 1e-3) / 1e9, 2),
             "fused_hbm_gbs": round(gbs, 1), "fused_frac_of_hbm": round(gbs / hbm, 4),
             "fused_algorithmic_bytes_per_px": 12,
+            "forward_alone_ms": round(ms_fwd, 4),
+            "forward_alone_frac_of_hbm": round(4.0 * px / (ms_fwd * 1e-3) / 1e9 / hbm, 4),
+            "backward_alone_ms": round(ms_bwd, 4),
+            "backward_alone_frac_of_hbm": round(8.0 * px / (ms_bwd * 1e-3) / 1e9 / hbm, 4),
             "fused_autograd_ms": round(ms_fused, 4),
             "unfused_autograd_ms": round(ms_unfused, 4),
             "plain_fp32_dwt_idwt_ms": round(ms_rt, 4),
@@ -1036,7 +1055,7 @@ def ragged_form(api, synth, dev, dense_fp32_gsamples):
                         f"levels 3..6, {px} px",
             "ms": round(ms, 4), "gsamples_s": round(px / (ms * 1e-3) / 1e9, 2),
             "hbm_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4),
-            "unit": {0: "64x128", 1: "32x256"}[unit], "blocks_per_sm": bps,
+            "unit": rep["unit_name"], "blocks_per_sm": bps,
             "autotune_ms": rep["timings"], "graph_replay": True, "queue_ok": ok,
             "round_trip_rel_l2": err,
             "per_image_loop_ms": round(ms_loop, 3),
@@ -1049,17 +1068,25 @@ def ragged_form(api, synth, dev, dense_fp32_gsamples):
 # ---------------------------------------------------------------------------
 def rows_once():
     """Each row's main operation once, on cases larger than L2, for an ncu
-    capture of the kernels behind every row: the ragged batch (first 64
-    images of the ragged shape list), the fused loss (32 x 3 x 512^2), 1D
-    signals (64 x 2^20: 8-level DWT + IDWT, shrinkage, one undecimated level,
-    Daubechies-4 bank), 2D shrinkage (4 x 4096^2), bf16 2D (64 x 2048^2,
-    4 levels) and a 512^3 volume (3 levels)."""
+    capture of the kernels behind every row: the headline image (4096^2
+    fp32, 5-level DWT + IDWT), the ragged batch (first 64 images of the
+    ragged shape list), the fused loss (32 x 3 x 512^2), 1D signals
+    (64 x 2^20: 8-level DWT + IDWT, shrinkage, one undecimated level,
+    Daubechies-4 bank, 8-tap lattice bank), 2D shrinkage (4 x 4096^2), bf16
+    2D (64 x 2048^2, 4 levels), uint8 -> bf16 analysis of the same batch and
+    a 512^3 volume (3 levels)."""
     import torch
     from paper_1002_2184_gb300 import api, build, synth
     from paper_1002_2184_gb300 import autograd as ad
     build.build()
     dev = torch.device("cuda", 0)
     torch.manual_seed(0)
+    x = torch.rand(4096, 4096, device=dev)
+    c, y = torch.empty_like(x), torch.empty_like(x)
+    ph = api.Plan(x, c, 5, y)
+    ph.dwt()
+    ph.idwt()
+    del x, c, y, ph
     rp = api.RaggedPlan(synth.ragged_shapes()[:64], dev, 0, 6)
     xr = rp.empty()
     xr.normal_()
@@ -1082,6 +1109,9 @@ def rows_once():
     api.swt1d(x, 1, out=torch.empty(64, 2, 1 << 20, device=dev))
     api.filter_dwt1d(x, 8, api.DAUBECHIES4, out=c)
     api.filter_idwt1d(c, 8, api.DAUBECHIES4, out=y)
+    k8 = lattice_taps([0.2, 0.5, -0.4, 0.9])
+    api.filter_dwt1d(x, 8, k8, out=c)
+    api.filter_idwt1d(c, 8, k8, out=y)
     del x, c, y
     x = torch.randn(4, 4096, 4096, device=dev)
     api.denoise2d(x, 5, 0.05, out=torch.empty_like(x))
@@ -1091,7 +1121,10 @@ def rows_once():
     pb = api.Plan(x, c, 4, y)
     pb.dwt()
     pb.idwt()
-    del x, c, y
+    u = (torch.rand(64, 2048, 2048, device=dev) * 255).to(torch.uint8)
+    pu = api.Plan(u, c, 4)
+    pu.dwt()
+    del x, c, y, u
     x = torch.randn(512, 512, 512, device=dev)
     c, y = torch.empty_like(x), torch.empty_like(x)
     api.dwt3d(x, 3, out=c)

@@ -30,7 +30,7 @@ HAAR_F32, HAAR_BF16, HAAR_F16, HAAR_U8, HAAR_F64 = 0, 1, 2, 3, 4
 HAAR_THRESH_SOFT, HAAR_THRESH_HARD = 0, 1
 
 # Ragged work-unit shapes.
-HAAR_UNIT_64x128, HAAR_UNIT_32x256 = 0, 1
+HAAR_UNIT_64x128, HAAR_UNIT_32x256, HAAR_UNIT_64x64, HAAR_UNIT_128x128 = 0, 1, 2, 3
 
 # Workspace-size operation codes.
 HAAR_OP_DWT_1D, HAAR_OP_IDWT_1D, HAAR_OP_DWT_2D, HAAR_OP_IDWT_2D = 0, 1, 2, 3

@@ -1,6 +1,7 @@
-"""Autotuner for the ragged-batch launch: picks the work-unit shape and the
-persistent grid size (blocks per SM) by timing every candidate on the
-caller's actual layout, and caches the choice as JSON.
+"""Autotuner for the ragged-batch launch: picks the work-unit shape (four
+shapes, three of them valid for six-level images) and the persistent grid
+size (resident warps per SM) by timing every candidate on the caller's
+actual layout, and caches the choice as JSON.
 
 The cache key is (input dtype, coefficient dtype, level-count range, a
 size class of the batch, SM count, device name); the size class buckets the
@@ -19,8 +20,26 @@ import torch
 from . import _lib
 from .api import RaggedPlan
 
-UNITS = {"64x128": _lib.HAAR_UNIT_64x128, "32x256": _lib.HAAR_UNIT_32x256}
-BLOCKS_PER_SM = (2, 3, 4, 6, 8)
+# unit name -> (unit code, unit height, warps per unit)
+UNITS = {"64x128": (_lib.HAAR_UNIT_64x128, 64, 8), "32x256": (_lib.HAAR_UNIT_32x256, 32, 8),
+         "64x64": (_lib.HAAR_UNIT_64x64, 64, 4), "128x128": (_lib.HAAR_UNIT_128x128, 128, 16)}
+# persistent grid sizes tried, as resident warps per SM (blocks per SM =
+# warps / warps per unit): the register cap allows 48
+WARPS_PER_SM = (16, 24, 32, 48)
+BLOCKS_PER_SM = tuple(sorted({w // n for _, _, n in UNITS.values() for w in WARPS_PER_SM}))
+
+
+def candidates(max_levels: int):
+    """(name, unit, blocks per SM) of every configuration eligible for a
+    batch whose deepest image has max_levels levels (a sixth level needs a
+    unit at least 64 rows high)."""
+    out = []
+    for name, (unit, uh, nw) in UNITS.items():
+        if max_levels > 5 and uh < 64:
+            continue
+        for w in WARPS_PER_SM:
+            out.append((name, unit, w // nw))
+    return out
 
 
 def default_cache_path() -> str:
@@ -78,20 +97,18 @@ def tune_ragged(items, device, x: torch.Tensor, coef_dtype=torch.float32, out_dt
     max_levels = max(L for _, _, L in items)
     timings = {}
     best = None
-    for uname, unit in UNITS.items():
-        if unit == _lib.HAAR_UNIT_32x256 and max_levels > 5:
-            continue
-        for bps in BLOCKS_PER_SM:
-            plan = RaggedPlan(items, device, unit, bps)
-            c = plan.empty(coef_dtype)
-            y = plan.empty(out_dtype)
-            ms = _time_round_trip(plan, x, c, y, reps)
-            timings[f"{uname}/bps{bps}"] = round(ms, 4)
-            if best is None or ms < best[0]:
-                best = (ms, unit, bps)
-            del plan, c, y
-    _, unit, bps = best
-    entry = {"unit": unit, "blocks_per_sm": bps, "ms": round(best[0], 4), "timings": timings}
+    for uname, unit, bps in candidates(max_levels):
+        plan = RaggedPlan(items, device, unit, bps)
+        c = plan.empty(coef_dtype)
+        y = plan.empty(out_dtype)
+        ms = _time_round_trip(plan, x, c, y, reps)
+        timings[f"{uname}/bps{bps}"] = round(ms, 4)
+        if best is None or ms < best[0]:
+            best = (ms, unit, bps, uname)
+        del plan, c, y
+    _, unit, bps, uname = best
+    entry = {"unit": unit, "unit_name": uname, "blocks_per_sm": bps, "ms": round(best[0], 4),
+             "timings": timings}
     if use_cache:
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)

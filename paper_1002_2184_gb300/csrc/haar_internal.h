@@ -92,10 +92,14 @@ struct RaggedArgs {
   void* out;
 };
 
-// Work-unit shapes (eight 32 x 32 warp blocks).
-enum RaggedUnit { kUnit64x128 = 0, kUnit32x256 = 1 };
-inline int unit_h(int u) { return u == kUnit64x128 ? 64 : 32; }
-inline int unit_w(int u) { return u == kUnit64x128 ? 128 : 256; }
+// Work-unit shapes (32 x 32 warp blocks: 8, 8, 4 and 16 of them).  A sixth
+// level needs units at least 64 rows high (two warp rows).
+enum RaggedUnit { kUnit64x128 = 0, kUnit32x256 = 1, kUnit64x64 = 2, kUnit128x128 = 3 };
+inline int unit_h(int u) { return u == kUnit32x256 ? 32 : u == kUnit128x128 ? 128 : 64; }
+inline int unit_w(int u) {
+  return u == kUnit32x256 ? 256 : u == kUnit64x64 ? 64 : 128;
+}
+inline bool unit_valid(int u) { return u >= kUnit64x128 && u <= kUnit128x128; }
 
 // Records the cudaError_t reported by haar_last_cuda_error() (per host thread).
 void set_last_cuda_error(int e);

@@ -1,8 +1,9 @@
 // haar_ragged.cuh -- one persistent launch over a ragged batch of images of
 // different sizes and level counts.
 //
-// The work is cut into units of UH x UW pixels (8 warps, one 32 x 32 block
-// per warp, the same per-warp bodies as the strided-batch kernels).  A plan
+// The work is cut into units of UH x UW pixels (one 32 x 32 block per warp,
+// the same per-warp bodies as the strided-batch kernels; 64 x 128, 32 x 256,
+// 64 x 64 or 128 x 128, picked by the autotuner).  A plan
 // lists, per image, its first unit index; blocks take units from a global
 // atomic counter, find the image by binary search, and transform.  The last
 // block to finish resets the counter, so the launch can be replayed (for
@@ -80,20 +81,21 @@ __device__ __forceinline__ Img2 ragged_image(const RaggedArgs& a, const RaggedIm
   return im;
 }
 
-// Both ragged kernels: FP32 arithmetic capped at 40 registers for 6 resident
-// blocks per SM (the 512-image batch: analysis 0.706 against 0.783 ms,
-// synthesis 0.711 against 0.741 ms); FP64 is not capped.
-template <typename Tin>
+// Both ragged kernels: FP32 arithmetic capped at 40 registers, 48 resident
+// warps per SM (8-warp units, the 512-image batch: analysis 0.706 against
+// 0.783 ms at 40 warps, synthesis 0.711 against 0.741 ms); FP64 is not
+// capped.  A unit of NW warps is one block of 32 NW threads.
+template <typename Tin, int NW>
 constexpr int ragged_min_blocks() {
-  return sizeof(typename AccT<Tin>::type) == 8 ? 1 : 6;
+  return sizeof(typename AccT<Tin>::type) == 8 ? 1 : (48 / NW > 0 ? 48 / NW : 1);
 }
 template <typename Tin, typename Tout, int UH, int UW>
-__global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_dwt2d(const RaggedArgs a) {
+__global__ void __launch_bounds__(UH * UW / 32, ragged_min_blocks<Tin, (UH / 32) * (UW / 32)>())
+    k_ragged_dwt2d(const RaggedArgs a) {
   pdl_wait();
   pdl_trigger();
   using A = typename AccT<Tin>::type;
   constexpr int WR = UH / 32, WC = UW / 32;
-  static_assert(WR * WC == 8, "a unit is eight 32 x 32 blocks");
   __shared__ long long s_unit;
   __shared__ int s_img;
   __shared__ A s5[WR][WC];
@@ -121,17 +123,21 @@ __global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_dwt2d(
       case 4: if (act) dwt_block32<Tin, Tout, 4>(im, y0, x0, lane); break;
       case 5: if (act) dwt_block32<Tin, Tout, 5>(im, y0, x0, lane); break;
       case 6:
-        if constexpr (WR == 2) {
+        if constexpr (WR % 2 == 0) {
+          // the unit's (WR / 2) x (WC / 2) blocks of 64 x 64 finish level 6
+          // from the LL5 values of their four warps
           const A l5 = act ? dwt_block32<Tin, Tout, 6>(im, y0, x0, lane) : A(0);
           if (lane == 0) s5[warp / WC][warp % WC] = l5;
           __syncthreads();
-          if (threadIdx.x < WC / 2) {
-            const int j = threadIdx.x;
-            const int64_t by0 = uy * 64, bx0 = ux * UW + 64 * j;
+          if (threadIdx.x < (WR / 2) * (WC / 2)) {
+            const int bi = threadIdx.x / (WC / 2), bj = threadIdx.x % (WC / 2);
+            const int64_t by0 = uy * UH + 64 * bi, bx0 = ux * UW + 64 * bj;
             if (by0 < r.h && bx0 < r.w)
-              dwt_level6<Tout>(im, s5[0][2 * j], s5[0][2 * j + 1], s5[1][2 * j],
-                               s5[1][2 * j + 1], by0, bx0);
+              dwt_level6<Tout>(im, s5[2 * bi][2 * bj], s5[2 * bi][2 * bj + 1],
+                               s5[2 * bi + 1][2 * bj], s5[2 * bi + 1][2 * bj + 1], by0, bx0);
           }
+          // (the barriers of ragged_next order these reads before the next
+          // unit rewrites s5)
         }
         break;
       default: break;
@@ -141,7 +147,8 @@ __global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_dwt2d(
 }
 
 template <typename Tin, typename Tout, int UH, int UW>
-__global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_idwt2d(const RaggedArgs a) {
+__global__ void __launch_bounds__(UH * UW / 32, ragged_min_blocks<Tin, (UH / 32) * (UW / 32)>())
+    k_ragged_idwt2d(const RaggedArgs a) {
   pdl_wait();
   pdl_trigger();
   constexpr int WC = UW / 32;
@@ -181,17 +188,23 @@ __global__ void __launch_bounds__(256, ragged_min_blocks<Tin>()) k_ragged_idwt2d
 template <typename Tin, typename Tout>
 cudaError_t ragged_t(bool fwd, const RaggedArgs& a, int unit, unsigned grid, cudaStream_t s) {
   if (a.total_units == 0 || grid == 0) return cudaSuccess;
+#define FH_RAGGED_UNIT(KERNEL)                                                                  \
+  switch (unit) {                                                                               \
+    case kUnit64x128: return launch_pdl(KERNEL<Tin, Tout, 64, 128>, grid, 256, s, a);          \
+    case kUnit32x256: return launch_pdl(KERNEL<Tin, Tout, 32, 256>, grid, 256, s, a);          \
+    case kUnit64x64: return launch_pdl(KERNEL<Tin, Tout, 64, 64>, grid, 128, s, a);            \
+    case kUnit128x128: return launch_pdl(KERNEL<Tin, Tout, 128, 128>, grid, 512, s, a);        \
+    default: return cudaErrorInvalidValue;                                                      \
+  }
   if (fwd) {
-    if (unit == kUnit64x128) return launch_pdl(k_ragged_dwt2d<Tin, Tout, 64, 128>, grid, 256, s, a);
-    return launch_pdl(k_ragged_dwt2d<Tin, Tout, 32, 256>, grid, 256, s, a);
+    FH_RAGGED_UNIT(k_ragged_dwt2d)
   }
   if constexpr (std::is_same<Tin, uint8_t>::value) {
     return cudaErrorInvalidValue;  // coefficients are never stored as uint8
   } else {
-    if (unit == kUnit64x128)
-      return launch_pdl(k_ragged_idwt2d<Tin, Tout, 64, 128>, grid, 256, s, a);
-    return launch_pdl(k_ragged_idwt2d<Tin, Tout, 32, 256>, grid, 256, s, a);
+    FH_RAGGED_UNIT(k_ragged_idwt2d)
   }
+#undef FH_RAGGED_UNIT
 }
 
 }  // namespace fh

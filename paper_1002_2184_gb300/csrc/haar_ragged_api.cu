@@ -119,7 +119,7 @@ int haar_ragged_plan_create(const haar_ragged_item* items, int64_t count, int un
   *plan = nullptr;
   if (count < 0 || (count > 0 && !items)) return HAAR_EINVAL;
   if (count > ((int64_t)1 << 31)) return HAAR_EINVAL;
-  if (unit != kUnit64x128 && unit != kUnit32x256) return HAAR_EINVAL;
+  if (!unit_valid(unit)) return HAAR_EINVAL;
   if (blocks_per_sm < 1 || blocks_per_sm > 32) return HAAR_EINVAL;
   haar_ragged_plan* p = new (std::nothrow) haar_ragged_plan;
   if (!p) return HAAR_EINVAL;
@@ -136,7 +136,7 @@ int haar_ragged_plan_create(const haar_ragged_item* items, int64_t count, int un
         it.in_row_stride > ((int64_t)1 << 40) || it.out_row_stride > ((int64_t)1 << 40))
       rc = HAAR_EINVAL;
     else if (it.h % 32 || it.w % 32 || (it.h & ((1 << it.levels) - 1)) ||
-             (it.w & ((1 << it.levels) - 1)) || (it.levels == 6 && unit == kUnit32x256))
+             (it.w & ((1 << it.levels) - 1)) || (it.levels == 6 && unit_h(unit) < 64))
       rc = HAAR_ESHAPE;
     if (rc) {
       delete p;

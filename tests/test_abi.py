@@ -154,8 +154,13 @@ def test_ragged_plan_validation(lib):
     assert _create(lib, [(64, 64, 7)])[0] == L.HAAR_EINVAL        # more than 6 levels
     assert _create(lib, [(64, 64, 0)])[0] == L.HAAR_EINVAL
     assert _create(lib, [(96, 64, 6)])[0] == L.HAAR_ESHAPE        # 96 % 64 != 0
-    assert _create(lib, [(64, 64, 6)], unit=1)[0] == L.HAAR_ESHAPE  # 6 levels need 64 x 128
+    assert _create(lib, [(64, 64, 6)], unit=1)[0] == L.HAAR_ESHAPE  # 6 levels need 64 rows
+    for unit in (0, 2, 3):                                            # units of >= 64 rows
+        rc, h = _create(lib, [(64, 64, 6)], unit=unit)
+        assert rc == L.HAAR_OK
+        lib.haar_ragged_plan_destroy(h)
     assert _create(lib, [(64, 64, 3)], unit=7)[0] == L.HAAR_EINVAL
+    assert _create(lib, [(64, 64, 3)], unit=4)[0] == L.HAAR_EINVAL
     assert _create(lib, [(64, 64, 3)], bps=0)[0] == L.HAAR_EINVAL
     bad = _items([(64, 64, 3)])
     bad[0].in_row_stride = 32
@@ -190,6 +195,20 @@ def test_ragged_plan_geometry(lib):
     assert rc == 0
     assert lib.haar_dwt_2d_ragged(h0, None, 0, None, 0, None, 0, None) == 0  # nothing to do
     lib.haar_ragged_plan_destroy(h0)
+
+
+@pytest.mark.parametrize("unit,expect", [(1, 2 + 2 + 4 * 1 + 1),   # 32 x 256 (5 levels max)
+                                         (2, 2 + 1 + 2 * 4 + 1),   # 64 x 64
+                                         (3, 1 + 1 + 1 * 2 + 1)])  # 128 x 128
+def test_ragged_unit_counts(lib, unit, expect):
+    """Each image is cut into ceil(h / UH) x ceil(w / UW) units."""
+    spec = [(64, 128, 5), (64, 64, 3), (128, 256, 5), (32, 32, 1)]
+    rc, h = _create(lib, spec, unit=unit)
+    assert rc == 0
+    units = ctypes.c_int64()
+    assert lib.haar_ragged_plan_info(h, ctypes.byref(units), None, None) == 0
+    assert units.value == expect
+    lib.haar_ragged_plan_destroy(h)
 
 
 # ---------------------------------------------------------------------------

@@ -27,10 +27,16 @@ SMALL = [(32, 32, 1), (64, 64, 6), (32, 96, 5), (96, 32, 3), (64, 128, 4), (128,
          (192, 256, 6), (32, 224, 5), (256, 192, 4), (64, 320, 6)]
 
 
-@pytest.mark.parametrize("unit", [_lib.HAAR_UNIT_64x128, _lib.HAAR_UNIT_32x256])
+UNITS = [_lib.HAAR_UNIT_64x128, _lib.HAAR_UNIT_32x256, _lib.HAAR_UNIT_64x64,
+         _lib.HAAR_UNIT_128x128]
+
+
+@pytest.mark.parametrize("unit", UNITS)
 @pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
 def test_ragged_small_matches_oracle(unit, dt):
-    items = SMALL if unit == _lib.HAAR_UNIT_64x128 else [
+    # the 32 x 256 unit takes at most 5 levels; every image of SMALL has sides
+    # that leave partial units for the larger shapes
+    items = SMALL if unit != _lib.HAAR_UNIT_32x256 else [
         (h, w, min(L, 5)) for h, w, L in SMALL]
     plan = api.RaggedPlan(items, DEV, unit, blocks_per_sm=2)
     x = fill(plan, dt, seed=31)
@@ -49,9 +55,10 @@ def test_ragged_small_matches_oracle(unit, dt):
     assert plan.status() == _lib.HAAR_OK
 
 
-def test_ragged_matches_strided_path_bitwise():
-    items = SMALL
-    plan = api.RaggedPlan(items, DEV)
+@pytest.mark.parametrize("unit", UNITS)
+def test_ragged_matches_strided_path_bitwise(unit):
+    items = SMALL if unit != _lib.HAAR_UNIT_32x256 else [(h, w, min(L, 5)) for h, w, L in SMALL]
+    plan = api.RaggedPlan(items, DEV, unit)
     x = fill(plan, torch.float32, seed=5)
     c = plan.empty()
     y = plan.empty()
@@ -143,8 +150,10 @@ def test_autotuner_picks_a_valid_config(tmp_path):
     x = fill(plan, torch.float32, seed=1)
     unit, bps, rep = autotune.tune_ragged(items, DEV, x, reps=2,
                                           cache_path=str(tmp_path / "cache.json"))
-    assert unit in (_lib.HAAR_UNIT_64x128, _lib.HAAR_UNIT_32x256)
+    assert unit in UNITS and unit != _lib.HAAR_UNIT_32x256  # SMALL has 6-level images
     assert bps in autotune.BLOCKS_PER_SM
+    shapes = {k.split("/")[0] for k in rep["timings"]}
+    assert shapes == {"64x128", "64x64", "128x128"}
     assert not rep["cached"] and rep["timings"]
     unit2, bps2, rep2 = autotune.tune_ragged(items, DEV, x, reps=2,
                                              cache_path=str(tmp_path / "cache.json"))
