@@ -485,6 +485,20 @@ __device__ __forceinline__ void idwt_prefetch(const Pass& p, int64_t b, int64_t 
 // blocks of the first wave only (p.pf_blocks), which are the ones that can
 // start while the previous kernel drains.
 // ---------------------------------------------------------------------------
+// Batch item and tile row / column of this block.  The launcher keeps the
+// tile count below 2^31, so 32-bit divisions suffice (a 64-bit division is
+// a long instruction sequence, paid by every warp).
+__device__ __forceinline__ void block_coords(const Pass& p, int64_t& b, int64_t& cy,
+                                             int64_t& cx) {
+  const uint32_t t = blockIdx.x, per = (uint32_t)(p.tiles_x * p.tiles_y);
+  const uint32_t tx = (uint32_t)p.tiles_x;
+  const uint32_t bb = t / per, rr = t - bb * per;
+  const uint32_t yy = rr / tx;
+  b = bb;
+  cy = yy;
+  cx = rr - yy * tx;
+}
+
 template <int WR, int WC, int WARPS>
 constexpr int fast_min_blocks() {
   return WARPS == 0 ? 1 : (WARPS / (WR * WC) > 0 ? WARPS / (WR * WC) : 1);
@@ -497,10 +511,9 @@ __global__ void __launch_bounds__(32 * WC * (L == 6 ? 2 : 1),
   using A = typename AccT<Tin>::type;
   constexpr int WR = (L == 6) ? 2 : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t per = p.tiles_x * p.tiles_y;
   const int64_t t = blockIdx.x;
-  const int64_t b = t / per, rr = t - b * per;
-  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
+  int64_t b, cy, cx;
+  block_coords(p, b, cy, cx);
   const int64_t by0 = cy * (32 * WR), bx0 = cx * (32 * WC);
   if (PF == 1 || (PF == 2 && t < p.pf_blocks)) dwt_prefetch<Tin, WR, WC>(p, b, by0, bx0);
   pdl_wait();
@@ -529,10 +542,9 @@ __global__ void __launch_bounds__(32 * WC, fast_min_blocks<1, WC, WARPS>())
     k_idwt2d_fast(const Pass p) {
   using A = typename AccT<Tin>::type;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t per = p.tiles_x * p.tiles_y;
   const int64_t t = blockIdx.x;
-  const int64_t b = t / per, rr = t - b * per;
-  const int64_t cy = rr / p.tiles_x, cx = rr - cy * p.tiles_x;
+  int64_t b, cy, cx;
+  block_coords(p, b, cy, cx);
   const int64_t by0 = cy * 32, bx0 = cx * (32 * WC);
   if (PF == 1 || (PF == 2 && t < p.pf_blocks)) idwt_prefetch<Tin, A, L, WC>(p, b, by0, bx0);
   pdl_wait();

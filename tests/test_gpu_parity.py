@@ -177,6 +177,32 @@ def test_uint8_input():
         assert_close(c, oracle.dwt2d(xn.astype(np.float64), 4), dt, f"u8 -> {dt}")
 
 
+# 1-byte images: sides that are multiples of 64 with 16-byte aligned rows take
+# the wide-lane analysis (4 x 16 pixels per lane), others the 4 x 8 one.  The
+# bytes are exact in FP32 and every kernel performs the same butterflies, so
+# the coefficients must equal those of the same image given as fp32.
+@pytest.mark.parametrize("b,h,w,levels", [(2, 32, 64, 1), (1, 64, 128, 2), (3, 96, 192, 3),
+                                          (2, 128, 256, 4), (1, 64, 320, 5), (1, 2048, 2048, 4),
+                                          (2, 64, 96, 4)])
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16, torch.float16])
+def test_uint8_analysis_equals_fp32_input_path(b, h, w, levels, dt):
+    xn = synth.quantize_u8(images(b, h, w, seed=h + w + levels))
+    x = torch.from_numpy(xn).to(DEV)
+    c = api.dwt2d(x, levels, dtype=dt)
+    assert torch.equal(c, api.dwt2d(x.float(), levels, dtype=dt))
+    assert_close(c, oracle.dwt2d(xn.astype(np.float64), levels), dt, f"u8 {b}x{h}x{w} L{levels}")
+
+
+def test_uint8_analysis_unaligned_rows():
+    """Rows starting 8 bytes past a 16-byte boundary take the 4 x 8 lane
+    layout (8-byte loads); the result is the same."""
+    base = torch.from_numpy(synth.quantize_u8(images(2, 64, 272, seed=12))).to(DEV)
+    x = base[:, :, 8:264]
+    c = api.dwt2d(x, 5, dtype=torch.bfloat16)
+    assert torch.equal(c, api.dwt2d(x.float(), 5, dtype=torch.bfloat16))
+    assert_close(c, oracle.dwt2d(host64(x), 5), torch.bfloat16, "u8 offset 8")
+
+
 def test_fp64_path():
     x = dev(images(2, 64, 128, seed=5), torch.float64)
     c = api.dwt2d(x, 6)
