@@ -1,15 +1,15 @@
-// haar_fast2d_u8.cuh -- 2D Fast Haar analysis of 1-byte images with a wide
-// micro-block per lane.
+// haar_fast2d_wide.cuh -- 2D Fast Haar analysis of 1- and 2-byte images
+// with a wide micro-block per lane.
 //
-// At one byte per input pixel the analysis moves about 3 bytes per pixel
-// (with 16-bit coefficients), so the register/warp-shuffle kernel of
-// haar_fast2d.cuh, whose per-lane costs (addresses, shuffles, predicates,
-// the coarse levels) are paid for every 4 x 8 pixels, runs out of
-// instruction issue before HBM is busy.  Here a lane owns 4 rows x 16
-// columns instead: one 16-byte load per row, level-1 details leave as 8
-// consecutive coefficients (one 16-byte store for 16-bit coefficients),
-// and every coarse level costs half as much per pixel.  A warp covers 32
-// rows x 64 columns (lane = 4 ty + tx, rows 4 ty .., columns 16 tx ..):
+// At one or two bytes per input pixel the analysis moves 3 or 4 bytes per
+// pixel, so the register/warp-shuffle kernel of haar_fast2d.cuh, whose
+// per-lane costs (addresses, shuffles, predicates, the coarse levels) are
+// paid for every 4 x 8 pixels, runs out of instruction issue before HBM is
+// busy.  Here a lane owns 4 rows x 16 columns instead: one or two 16-byte
+// loads per row, level-1 details leave as 8 consecutive coefficients (one
+// 16-byte store for 16-bit coefficients), and every coarse level costs half
+// as much per pixel.  A warp covers 32 rows x 64 columns (lane = 4 ty + tx,
+// rows 4 ty .., columns 16 tx ..):
 //   level 1, 2: in the lane (2 x 8 -> 1 x 4 low-pass values);
 //   level 3:    pairs of columns in the lane, rows with lane ^ 4;
 //   level 4:    the lane's two level-3 columns, rows with lane ^ 8;
@@ -23,27 +23,66 @@
 
 namespace fh {
 
-// 16 consecutive bytes -> 16 floats (exact).
-__device__ __forceinline__ void unpack16(const uint4 u, float v[16]) {
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+// 16 consecutive input samples of one row, kept in their storage type until
+// the row pair is transformed: one 16-byte load for bytes, two for 16-bit
+// samples.
+template <typename Tin> struct Row16 {
+  uint4 u[sizeof(Tin)];
+};
+template <typename Tin>
+__device__ __forceinline__ void ld_row16(const Tin* p, Row16<Tin>& r) {
+#pragma unroll
+  for (int k = 0; k < (int)sizeof(Tin); ++k) r.u[k] = __ldg(reinterpret_cast<const uint4*>(p) + k);
+}
+__device__ __forceinline__ void unpack16(const Row16<uint8_t>& r, float v[16]) {
+  const uint32_t w[4] = {r.u[0].x, r.u[0].y, r.u[0].z, r.u[0].w};
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[4 * q + k] = u8_to_f32(w[q], k);
 }
+template <typename H2>
+__device__ __forceinline__ float2 h2f(uint32_t w);
+template <>
+__device__ __forceinline__ float2 h2f<__nv_bfloat162>(uint32_t w) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+}
+template <>
+__device__ __forceinline__ float2 h2f<__half2>(uint32_t w) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+template <typename T, typename H2>
+__device__ __forceinline__ void unpack16_h(const Row16<T>& r, float v[16]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t w[4] = {r.u[k].x, r.u[k].y, r.u[k].z, r.u[k].w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = h2f<H2>(w[q]);
+      v[8 * k + 2 * q] = f.x;
+      v[8 * k + 2 * q + 1] = f.y;
+    }
+  }
+}
+__device__ __forceinline__ void unpack16(const Row16<__nv_bfloat16>& r, float v[16]) {
+  unpack16_h<__nv_bfloat16, __nv_bfloat162>(r, v);
+}
+__device__ __forceinline__ void unpack16(const Row16<__half>& r, float v[16]) {
+  unpack16_h<__half, __half2>(r, v);
+}
 
 // Analysis of one 32 x 64 block by one warp, levels 1..L (L <= 5).
-template <typename Tout, int L>
-__device__ __forceinline__ void dwt_block_u8w(const Img2& im, int64_t y0, int64_t x0, int lane) {
+template <typename Tin, typename Tout, int L>
+__device__ __forceinline__ void dwt_block_w(const Img2& im, int64_t y0, int64_t x0, int lane) {
   static_assert(L >= 1 && L <= 5, "a 32-row warp block fuses at most 5 levels");
   using A = float;
   const int tx = lane & 3, ty = lane >> 2;
   const Bands<Tout> out{static_cast<Tout*>(im.dst), im.d_rs, im.h, im.w};
   const int64_t py = y0 + 4 * ty, px = x0 + 16 * tx;
-  const uint8_t* src = static_cast<const uint8_t*>(im.src) + py * im.s_rs + px;
-  uint4 raw[4];
+  const Tin* src = static_cast<const Tin*>(im.src) + py * im.s_rs + px;
+  Row16<Tin> raw[4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) raw[r] = __ldg(reinterpret_cast<const uint4*>(src + r * im.s_rs));
+  for (int r = 0; r < 4; ++r) ld_row16(src + r * im.s_rs, raw[r]);
 
   // ---- level 1: two row pairs of eight 2x2 blocks ----
   A l1[2][8];
@@ -137,37 +176,38 @@ __device__ __forceinline__ void dwt_block_u8w(const Img2& im, int64_t y0, int64_
 // Blocks of WC warps side by side (WC x 64 columns); WARPS resident warps
 // per SM set the register cap.  The input rows of a block are at least 128
 // bytes, so the L2 warm-up asks for whole lines.
-template <typename Tout, int L, int WC, int WARPS, int PF>
+template <typename Tin, typename Tout, int L, int WC, int WARPS, int PF>
 __global__ void __launch_bounds__(32 * WC, fast_min_blocks<1, WC, WARPS>())
-    k_dwt2d_u8w(const Pass p) {
+    k_dwt2d_w(const Pass p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t t = blockIdx.x;
   int64_t b, cy, cx;
   block_coords(p, b, cy, cx);
   const int64_t by0 = cy * 32, bx0 = cx * (64 * WC);
-  if (PF == 1 || (PF == 2 && t < p.pf_blocks)) dwt_prefetch<uint8_t, 1, 2 * WC>(p, b, by0, bx0);
+  if (PF == 1 || (PF == 2 && t < p.pf_blocks)) dwt_prefetch<Tin, 1, 2 * WC>(p, b, by0, bx0);
   pdl_wait();
   pdl_trigger();
   const int64_t x0 = bx0 + warp * 64;
   if (by0 < p.h && x0 < p.w)
-    dwt_block_u8w<Tout, L>(pass_image<uint8_t, Tout>(p, b, true), by0, x0, lane);
+    dwt_block_w<Tin, Tout, L>(pass_image<Tin, Tout>(p, b, true), by0, x0, lane);
 }
 
 // Whether a pass can take the wide kernel: width a multiple of 64, at most 5
 // levels, the low band in the coefficient array, image rows and the
 // coefficient rows 16-byte aligned (16-byte loads; 8 coefficients per
 // store).
-template <typename Tout>
-inline bool u8w_ok(const Pass& p) {
+template <typename Tin, typename Tout>
+inline bool wide_ok(const Pass& p) {
   const auto al16 = [](const void* q, int64_t bs, int64_t rs, int esz) {
     return ((uintptr_t)q % 16) == 0 && ((bs * esz) % 16) == 0 && ((rs * esz) % 16) == 0;
   };
-  return p.w % 64 == 0 && p.levels <= 5 && !p.ll_acc && al16(p.src, p.s_bs, p.s_rs, 1) &&
+  return p.w % 64 == 0 && p.levels <= 5 && !p.ll_acc &&
+         al16(p.src, p.s_bs, p.s_rs, (int)sizeof(Tin)) &&
          al16(p.dst, p.d_bs, p.d_rs, (int)sizeof(Tout));
 }
 
-template <typename Tout, int WC, int WARPS, int PF>
-cudaError_t dwt2d_u8w_cfg(Pass p, cudaStream_t s) {
+template <typename Tin, typename Tout, int WC, int WARPS, int PF>
+cudaError_t dwt2d_w_cfg(Pass p, cudaStream_t s) {
   const int CW = 64 * WC;
   p.tiles_x = (p.w + CW - 1) / CW;
   p.tiles_y = (p.h + 31) / 32;
@@ -178,11 +218,11 @@ cudaError_t dwt2d_u8w_cfg(Pass p, cudaStream_t s) {
   const unsigned g = (unsigned)p.ntiles;
   const unsigned nt = 32 * WC;
   switch (p.levels) {
-    case 1: return launch_pdl(k_dwt2d_u8w<Tout, 1, WC, WARPS, PF>, g, nt, s, p);
-    case 2: return launch_pdl(k_dwt2d_u8w<Tout, 2, WC, WARPS, PF>, g, nt, s, p);
-    case 3: return launch_pdl(k_dwt2d_u8w<Tout, 3, WC, WARPS, PF>, g, nt, s, p);
-    case 4: return launch_pdl(k_dwt2d_u8w<Tout, 4, WC, WARPS, PF>, g, nt, s, p);
-    case 5: return launch_pdl(k_dwt2d_u8w<Tout, 5, WC, WARPS, PF>, g, nt, s, p);
+    case 1: return launch_pdl(k_dwt2d_w<Tin, Tout, 1, WC, WARPS, PF>, g, nt, s, p);
+    case 2: return launch_pdl(k_dwt2d_w<Tin, Tout, 2, WC, WARPS, PF>, g, nt, s, p);
+    case 3: return launch_pdl(k_dwt2d_w<Tin, Tout, 3, WC, WARPS, PF>, g, nt, s, p);
+    case 4: return launch_pdl(k_dwt2d_w<Tin, Tout, 4, WC, WARPS, PF>, g, nt, s, p);
+    case 5: return launch_pdl(k_dwt2d_w<Tin, Tout, 5, WC, WARPS, PF>, g, nt, s, p);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,7 +7,7 @@
 #include "haar_internal.h"
 #include "haar_fast1d.cuh"
 #include "haar_fast2d.cuh"
-#include "haar_fast2d_u8.cuh"
+#include "haar_fast2d_wide.cuh"
 #include "haar_ragged.cuh"
 #include "haar_kernels.cuh"
 
@@ -99,13 +99,13 @@ inline unsigned grid_for(int64_t ntiles, int grid_cap) {
   return (unsigned)g;
 }
 
-// The wide-lane analysis of 1-byte images (haar_fast2d_u8.cuh): 2-warp
-// blocks (a block row is one 128-byte line), 32 resident warps per SM (64
-// registers), L2 warm-up in the first wave.
+// The wide-lane analysis of 1- and 2-byte images (haar_fast2d_wide.cuh):
+// 2-warp blocks (a block row is one or two 128-byte lines), 32 resident warps
+// per SM (64 registers), L2 warm-up in the first wave.
 template <typename Tin, typename Tout>
 cudaError_t dwt2d_t(Pass p, int cfg, bool vec, int grid_cap, cudaStream_t s) {
-  if constexpr (std::is_same<Tin, uint8_t>::value) {
-    if (cfg == kFast && u8w_ok<Tout>(p)) return dwt2d_u8w_cfg<Tout, 2, 32, 2>(p, s);
+  if constexpr (sizeof(Tin) <= 2) {
+    if (cfg == kFast && wide_ok<Tin, Tout>(p)) return dwt2d_w_cfg<Tin, Tout, 2, 32, 2>(p, s);
   }
   if (cfg == kFast) return dwt2d_fast_t<Tin, Tout>(p, s);
   const int TH = vec ? tile_h(cfg) : 64, TW = vec ? tile_w(cfg) : 64;

@@ -193,6 +193,18 @@ def test_uint8_analysis_equals_fp32_input_path(b, h, w, levels, dt):
     assert_close(c, oracle.dwt2d(xn.astype(np.float64), levels), dt, f"u8 {b}x{h}x{w} L{levels}")
 
 
+@pytest.mark.parametrize("b,h,w,levels", [(2, 32, 64, 1), (1, 64, 128, 2), (3, 96, 192, 3),
+                                          (2, 128, 256, 4), (1, 64, 320, 5), (2, 64, 96, 4)])
+@pytest.mark.parametrize("tin", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+def test_half_analysis_equals_fp32_input_path(b, h, w, levels, tin, dt):
+    """16-bit images (wide-lane analysis for sides multiple of 64): exact in
+    FP32, so the coefficients equal those of the same values given as fp32."""
+    x = dev(images(b, h, w, seed=h * 3 + w + levels), tin)
+    c = api.dwt2d(x, levels, dtype=dt)
+    assert torch.equal(c, api.dwt2d(x.float(), levels, dtype=dt))
+
+
 def test_uint8_analysis_unaligned_rows():
     """Rows starting 8 bytes past a 16-byte boundary take the 4 x 8 lane
     layout (8-byte loads); the result is the same."""
