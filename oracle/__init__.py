@@ -254,7 +254,7 @@ def denoise_loss(x, levels: int, t: float, lam: float):
     return mse + lam * l1, mse, l1
 
 
-def denoise_loss_grad(x, levels: int, t: float, lam: float) -> np.ndarray:
+def denoise_loss_grad(x, levels: int, t: float, lam: float, keep=None) -> np.ndarray:
     """Closed-form gradient of :func:`denoise_loss` with respect to x.
 
     With W the orthonormal DWT (so IDWT = W^T and its adjoint is W):
@@ -262,7 +262,13 @@ def denoise_loss_grad(x, levels: int, t: float, lam: float) -> np.ndarray:
       g_s  = W g_xr + lam * sign(s) * mask / n_d
       g_c  = g_s * [|c| > t]
       g_x  = W^T g_c - 2 (xr - x) / n
-    """
+
+    keep: optionally the decision [|c| > t] as the implementation under test
+    took it, in its own precision.  The gradient jumps where |c| crosses t,
+    so a coefficient within rounding of t may be decided differently in FP32
+    and FP64; a comparison element by element needs both sides to decide the
+    same way, and the mask replaces the FP64 comparison here (the values are
+    still FP64)."""
     x = _f64(x)
     h, w = x.shape[-2:]
     n = x.size
@@ -273,7 +279,7 @@ def denoise_loss_grad(x, levels: int, t: float, lam: float) -> np.ndarray:
     n_d = int(mask.sum())
     g_xr = 2.0 * (xr - x) / n
     g_s = dwt2d(g_xr, levels) + lam * np.sign(s) * mask / n_d
-    g_c = g_s * (np.abs(c) > t)
+    g_c = g_s * ((np.abs(c) > t) if keep is None else np.asarray(keep, dtype=bool))
     return idwt2d(g_c, levels) - g_xr
 
 
@@ -383,27 +389,32 @@ def iswt1d(c, levels: int) -> np.ndarray:
 # low band, transform back.
 # --------------------------------------------------------------------------
 
-def shrink(d, t: float, hard: bool = False) -> np.ndarray:
+def shrink(d, t: float, hard: bool = False, keep=None) -> np.ndarray:
+    """Soft: sign(d) max(|d| - t, 0).  Hard: d [|d| > t]; keep optionally
+    gives that decision as the implementation under test took it in its own
+    precision (hard shrinkage jumps at |d| = t, so both sides of an
+    element-by-element comparison must decide alike)."""
     d = _f64(d)
     if hard:
-        return np.where(np.abs(d) > t, d, 0.0)
+        k = (np.abs(d) > t) if keep is None else np.asarray(keep, dtype=bool)
+        return np.where(k, d, 0.0)
     return np.sign(d) * np.maximum(np.abs(d) - t, 0.0)
 
 
-def denoise1d(x, levels: int, t: float, hard: bool = False) -> np.ndarray:
+def denoise1d(x, levels: int, t: float, hard: bool = False, keep=None) -> np.ndarray:
     x = _f64(x)
     c = dwt1d(x, levels)
     mask = np.broadcast_to(detail_mask_1d(x.shape[-1], levels), c.shape)
-    c = np.where(mask, shrink(c, t, hard), c)
+    c = np.where(mask, shrink(c, t, hard, keep), c)
     return idwt1d(c, levels)
 
 
-def denoise2d(x, levels: int, t: float, hard: bool = False) -> np.ndarray:
+def denoise2d(x, levels: int, t: float, hard: bool = False, keep=None) -> np.ndarray:
     x = _f64(x)
     h, w = x.shape[-2:]
     c = dwt2d(x, levels)
     mask = np.broadcast_to(detail_mask_2d(h, w, levels), c.shape)
-    c = np.where(mask, shrink(c, t, hard), c)
+    c = np.where(mask, shrink(c, t, hard, keep), c)
     return idwt2d(c, levels)
 
 

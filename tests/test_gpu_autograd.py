@@ -64,6 +64,28 @@ def test_gradcheck_fused_loss_fp64():
                                     eps=1e-6, atol=1e-8)
 
 
+def gpu_decision(x: torch.Tensor, levels: int, t: float) -> np.ndarray:
+    """[|c| > t] as the kernels decide it: on the FP32 coefficients (the
+    analysis inside the loss kernels performs the same operations as the
+    separate one) against the threshold rounded to FP32.  The gradient jumps
+    where |c| crosses t, so the oracle is handed this decision for an
+    element-by-element comparison."""
+    c = api.dwt2d(x, levels)
+    return (c.abs() > torch.tensor(t, dtype=torch.float32)).cpu().numpy()
+
+
+def assert_grad_close(g: torch.Tensor, ref: np.ndarray, what: str):
+    """rel-L2 <= 1e-5 and every element within 1e-5 of the largest gradient
+    magnitude (the FP32 analysis, map and synthesis each round; the loss
+    scale 2/n leaves the gradient near 1e-9, so the bound is relative)."""
+    got = g.detach().double().cpu().numpy()
+    err = oracle.rel_l2(got, ref)
+    mx = oracle.max_abs(got, ref)
+    scale = float(np.max(np.abs(ref)))
+    assert err <= 1e-5, f"{what}: gradient rel-L2 {err:.3e}"
+    assert mx <= 1e-5 * scale, f"{what}: gradient max-abs {mx:.3e} (scale {scale:.3e})"
+
+
 @pytest.mark.parametrize("fused", [True, False])
 def test_loss_and_gradient_match_oracle_fp32(fused):
     """Config-shaped batch (reduced batch) in fp32 against the oracle's loss
@@ -74,9 +96,9 @@ def test_loss_and_gradient_match_oracle_fp32(fused):
     loss.backward()
     xn = x.detach().double().cpu().numpy()
     ref_loss, _, _ = oracle.denoise_loss(xn, 3, 0.05, 1e-3)
-    ref_g = oracle.denoise_loss_grad(xn, 3, 0.05, 1e-3)
+    ref_g = oracle.denoise_loss_grad(xn, 3, 0.05, 1e-3, keep=gpu_decision(x.detach(), 3, 0.05))
     assert abs(float(loss.detach()) - ref_loss) <= 1e-5 * abs(ref_loss)
-    assert oracle.rel_l2(x.grad.double().cpu().numpy(), ref_g) <= 1e-5
+    assert_grad_close(x.grad, ref_g, "fused" if fused else "unfused")
 
 
 def test_fused_equals_unfused_fp32():
@@ -103,8 +125,9 @@ def test_gradient_workload_full_size():
     xn = x.detach().double().cpu().numpy()
     ref_loss, _, _ = oracle.denoise_loss(xn, cfg.levels, cfg.threshold, cfg.l1_weight)
     assert abs(float(loss.detach()) - ref_loss) <= 1e-5 * abs(ref_loss)
-    ref_g = oracle.denoise_loss_grad(xn, cfg.levels, cfg.threshold, cfg.l1_weight)
-    assert oracle.rel_l2(x.grad.double().cpu().numpy(), ref_g) <= 1e-5
+    ref_g = oracle.denoise_loss_grad(xn, cfg.levels, cfg.threshold, cfg.l1_weight,
+                                     keep=gpu_decision(x.detach(), cfg.levels, cfg.threshold))
+    assert_grad_close(x.grad, ref_g, "full-size batch")
 
 
 def test_soft_threshold_and_l1_pieces():

@@ -518,6 +518,26 @@ def test_hard_shrink_keeps_large_details_exactly():
     assert np.allclose(np.delete(d, [4, 5]), 0.0, atol=1e-15)
 
 
+def test_decision_masks_reproduce_the_default_paths():
+    """Passing the FP64 decision itself as `keep` changes nothing; a flipped
+    decision changes exactly the coefficients it names."""
+    rng = synth.rng(15, 0)
+    x = rng.standard_normal((2, 256))
+    c = oracle.dwt1d(x, 4)
+    keep = np.abs(c) > 0.7
+    assert np.array_equal(oracle.denoise1d(x, 4, 0.7, True, keep),
+                          oracle.denoise1d(x, 4, 0.7, True))
+    im = rng.standard_normal((1, 2, 32, 32)) * 0.2
+    ci = oracle.dwt2d(im, 3)
+    k2 = np.abs(ci) > 0.05
+    assert np.array_equal(oracle.denoise_loss_grad(im, 3, 0.05, 1e-3, k2),
+                          oracle.denoise_loss_grad(im, 3, 0.05, 1e-3))
+    flipped = keep.copy()
+    flipped[0, 200] = ~flipped[0, 200]
+    d = oracle.dwt1d(oracle.denoise1d(x, 4, 0.7, True, flipped) - oracle.denoise1d(x, 4, 0.7, True), 4)
+    assert np.count_nonzero(np.abs(d) > 1e-12) == 1 and abs(abs(d[0, 200]) - abs(c[0, 200])) < 1e-12
+
+
 # --------------------------------------------------------------------------
 # Undecimated (stationary) transform.
 # --------------------------------------------------------------------------
