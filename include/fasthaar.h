@@ -170,13 +170,19 @@ typedef struct {
   int64_t batch_stride, plane_stride, row_stride; /* elements */
 } haar_desc3;
 
-/* Workspace of a 3D transform deeper than 3 levels (3 fuse per launch). */
+/* Workspace of a 3D transform: the tiled kernels need one for more than 3
+ * levels (3 fuse per launch); volumes they cannot take (below) need the low
+ * band of every level but the last (about 1/7 of the volume, accumulator
+ * type).  The answer is for x's layout; a transform between two arrays needs
+ * the larger of the answers for both descriptors. */
 int haar_workspace_size_3d(const haar_desc3 *x, int levels, size_t *bytes);
 
-/* 3D analysis / synthesis.  d, h, w divisible by 2^levels; w a multiple of 8
- * (rows move 8 samples at a time), and every chained pass must keep w >> 3k
- * a multiple of 8; rows 16-byte aligned.  dtypes: equal storage types, or
- * F32 with BF16/F16 (either direction); F64 only with F64. */
+/* 3D analysis / synthesis.  d, h, w divisible by 2^levels.  The tiled
+ * kernels take volumes whose width at every pass of 3 levels is a multiple
+ * of 8 and whose rows, planes and batch items are 16-byte aligned in both
+ * arrays; any other volume runs a generic kernel per level (element by
+ * element, same results).  dtypes: equal storage types, or F32 with
+ * BF16/F16 (either direction); F64 only with F64. */
 int haar_dwt_3d(const haar_desc3 *x, const haar_desc3 *coef, int levels, void *workspace,
                 size_t workspace_bytes, void *cuda_stream);
 int haar_idwt_3d(const haar_desc3 *coef, const haar_desc3 *x, int levels, void *workspace,

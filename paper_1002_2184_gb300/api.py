@@ -401,10 +401,16 @@ def describe3(t: torch.Tensor) -> _lib.HaarDesc3:
 def _run3(fn_name: str, src: torch.Tensor, dst: torch.Tensor, levels: int) -> torch.Tensor:
     lib = _lib.load()
     ds, dd = describe3(src), describe3(dst)
-    n = ctypes.c_size_t(0)
-    _lib.check(lib.haar_workspace_size_3d(ctypes.byref(ds), levels, ctypes.byref(n)),
-               "haar_workspace_size_3d")
-    ws = torch.empty(n.value, dtype=torch.uint8, device=src.device) if n.value else None
+    # the workspace depends on which kernels take the transform, which both
+    # arrays' layouts decide: the larger of the two answers covers it
+    need = 0
+    for d in (ds, dd):
+        n = ctypes.c_size_t(0)
+        _lib.check(lib.haar_workspace_size_3d(ctypes.byref(d), levels, ctypes.byref(n)),
+                   "haar_workspace_size_3d")
+        need = max(need, n.value)
+    n = ctypes.c_size_t(need)
+    ws = torch.empty(need, dtype=torch.uint8, device=src.device) if need else None
     with torch.cuda.device(src.device):
         rc = getattr(lib, fn_name)(ctypes.byref(ds), ctypes.byref(dd), levels,
                                    ws.data_ptr() if ws is not None else None, n.value,

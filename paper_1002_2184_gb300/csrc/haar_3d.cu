@@ -13,6 +13,8 @@
 // detail octants with 16-byte stores; deeper levels run in shared memory on
 // the tile's low band, which is then scattered to the global layout.
 // Transforms deeper than three levels chain launches through a workspace.
+// Volumes the tiles cannot take (width not a multiple of 8 at some pass,
+// unaligned rows) run a generic kernel per level instead.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -437,6 +439,141 @@ cudaError_t dispatch3d(bool fwd, int tin, int tout, const Pass3& p, cudaStream_t
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// Generic path for the volumes the tiled kernels cannot take (a width that
+// is not a multiple of 8, rows, planes or batch items that are not 16-byte
+// aligned, or a deep pass on a region narrower than 8): one thread per
+// 2 x 2 x 2 block, one launch per level, every element loaded and stored on
+// its own, the low band of each level in the workspace.  The butterflies are
+// fwd_oct / inv_oct, as in the tiled kernels.
+// ---------------------------------------------------------------------------
+struct Lvl3 {
+  void* io;  // the level's full-resolution side: input (analysis) / output (synthesis)
+  int64_t i_bs, i_zs, i_rs;
+  void* coef;  // details of every level (octant layout)
+  int64_t c_bs, c_zs, c_rs;
+  void* low;  // this level's LLL: output (analysis) / input (synthesis)
+  int64_t l_bs, l_zs, l_rs;
+  int64_t batch, d, h, w;  // the level's full-resolution region
+};
+
+// Block index t -> batch item b and block (i, j, k) of the half-size region.
+__device__ __forceinline__ void gen3_index(const Lvl3& q, int64_t t, int64_t& b, int64_t& i,
+                                           int64_t& j, int64_t& k) {
+  const int64_t h2 = q.h >> 1, w2 = q.w >> 1, per = (q.d >> 1) * h2 * w2;
+  b = t / per;
+  int64_t r = t - b * per;
+  i = r / (h2 * w2);
+  r -= i * h2 * w2;
+  j = r / w2;
+  k = r - j * w2;
+}
+
+template <typename TS, typename TC, typename TL>
+__global__ void __launch_bounds__(256) k_dwt3d_gen(const Lvl3 q) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename AccT<TS>::type;
+  const int64_t d2 = q.d >> 1, h2 = q.h >> 1, w2 = q.w >> 1;
+  const int64_t total = q.batch * d2 * h2 * w2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b, i, j, k;
+    gen3_index(q, t, b, i, j, k);
+    const TS* src = static_cast<const TS*>(q.io) + b * q.i_bs + 2 * i * q.i_zs + 2 * j * q.i_rs +
+                    2 * k;
+    A v[2][2][2], o[2][2][2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+      for (int y = 0; y < 2; ++y)
+#pragma unroll
+        for (int x = 0; x < 2; ++x) v[z][y][x] = ld_scalar(src + z * q.i_zs + y * q.i_rs + x);
+    fwd_oct(v, o);
+    TC* c = static_cast<TC*>(q.coef) + b * q.c_bs;
+#pragma unroll
+    for (int oc = 1; oc < 8; ++oc) {
+      const int bz = oc >> 2, by = (oc >> 1) & 1, bx = oc & 1;
+      st_scalar(c + (bz * d2 + i) * q.c_zs + (by * h2 + j) * q.c_rs + bx * w2 + k, o[bz][by][bx]);
+    }
+    st_scalar(static_cast<TL*>(q.low) + b * q.l_bs + i * q.l_zs + j * q.l_rs + k, o[0][0][0]);
+  }
+}
+
+template <typename TL, typename TC, typename TD>
+__global__ void __launch_bounds__(256) k_idwt3d_gen(const Lvl3 q) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename AccT<TC>::type;
+  const int64_t d2 = q.d >> 1, h2 = q.h >> 1, w2 = q.w >> 1;
+  const int64_t total = q.batch * d2 * h2 * w2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b, i, j, k;
+    gen3_index(q, t, b, i, j, k);
+    const TC* c = static_cast<const TC*>(q.coef) + b * q.c_bs;
+    A o[2][2][2], v[2][2][2];
+    o[0][0][0] = ld_scalar(static_cast<const TL*>(q.low) + b * q.l_bs + i * q.l_zs + j * q.l_rs + k);
+#pragma unroll
+    for (int oc = 1; oc < 8; ++oc) {
+      const int bz = oc >> 2, by = (oc >> 1) & 1, bx = oc & 1;
+      o[bz][by][bx] = ld_scalar(c + (bz * d2 + i) * q.c_zs + (by * h2 + j) * q.c_rs + bx * w2 + k);
+    }
+    inv_oct(o, v);
+    TD* dst = static_cast<TD*>(q.io) + b * q.i_bs + 2 * i * q.i_zs + 2 * j * q.i_rs + 2 * k;
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+      for (int y = 0; y < 2; ++y)
+#pragma unroll
+        for (int x = 0; x < 2; ++x) st_scalar(dst + z * q.i_zs + y * q.i_rs + x, v[z][y][x]);
+  }
+}
+
+// One level of the generic path.  ta / tb / tc: dtypes of (analysis) the
+// input, the coefficients and the low band, or (synthesis) the low band, the
+// coefficients and the output.
+template <typename X, typename Y, typename Z>
+cudaError_t gen3_go(bool fwd, const Lvl3& q, unsigned grid, cudaStream_t s) {
+  if (fwd) return launch_pdl(k_dwt3d_gen<X, Y, Z>, grid, 256, s, q);
+  return launch_pdl(k_idwt3d_gen<X, Y, Z>, grid, 256, s, q);
+}
+template <typename X, typename Y>
+cudaError_t gen3_z(bool fwd, int tc, const Lvl3& q, unsigned grid, cudaStream_t s) {
+  switch (tc) {
+    case HAAR_F32: return gen3_go<X, Y, float>(fwd, q, grid, s);
+    case HAAR_BF16: return gen3_go<X, Y, __nv_bfloat16>(fwd, q, grid, s);
+    case HAAR_F16: return gen3_go<X, Y, __half>(fwd, q, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+template <typename X>
+cudaError_t gen3_y(bool fwd, int tb, int tc, const Lvl3& q, unsigned grid, cudaStream_t s) {
+  switch (tb) {
+    case HAAR_F32: return gen3_z<X, float>(fwd, tc, q, grid, s);
+    case HAAR_BF16: return gen3_z<X, __nv_bfloat16>(fwd, tc, q, grid, s);
+    case HAAR_F16: return gen3_z<X, __half>(fwd, tc, q, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t dispatch3d_gen(bool fwd, int ta, int tb, int tc, const Lvl3& q, cudaStream_t s) {
+  const int64_t total = q.batch * (q.d >> 1) * (q.h >> 1) * (q.w >> 1);
+  if (total == 0) return cudaSuccess;
+  int64_t g = (total + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;  // grid-stride beyond 32 blocks per SM
+  const unsigned grid = (unsigned)g;
+  if (ta == HAAR_F64 || tb == HAAR_F64 || tc == HAAR_F64)
+    return (ta == HAAR_F64 && tb == HAAR_F64 && tc == HAAR_F64)
+               ? gen3_go<double, double, double>(fwd, q, grid, s)
+               : cudaErrorInvalidValue;
+  switch (ta) {
+    case HAAR_F32: return gen3_y<float>(fwd, tb, tc, q, grid, s);
+    case HAAR_BF16: return gen3_y<__nv_bfloat16>(fwd, tb, tc, q, grid, s);
+    case HAAR_F16: return gen3_y<__half>(fwd, tb, tc, q, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace fh
 
 using namespace fh;
@@ -492,6 +629,96 @@ size_t ws3(const haar_desc3* x, int levels, size_t off[64]) {
   return tot;
 }
 
+// Whether the tiled kernels take a transform: every pass's region at least
+// 8 wide and a multiple of 8 (rows move 8 samples at a time), and the rows,
+// planes and batch items of both arrays 16-byte aligned.
+bool tiled3_ok(const haar_desc3* in, const haar_desc3* out, int levels) {
+  auto al = [](const haar_desc3* d) {
+    const int esz = dt_size(d->dtype);
+    return ((uintptr_t)d->ptr % 16) == 0 && (d->row_stride * esz) % 16 == 0 &&
+           (d->plane_stride * esz) % 16 == 0 && (d->batch_stride * esz) % 16 == 0;
+  };
+  if (!al(in) || !al(out)) return false;
+  int lv[64], cum[65];
+  const int np = plan_passes3(levels, lv, cum);
+  for (int k = 0; k < np; ++k)
+    if ((in->w >> cum[k]) % 8) return false;
+  return true;
+}
+
+// Workspace of the generic path: the low band of every level but the last
+// (accumulator type), one region each.
+size_t ws_gen3(const haar_desc3* x, int levels, size_t off[64]) {
+  const size_t esz = x->dtype == HAAR_F64 ? 8 : 4;
+  size_t tot = 0;
+  for (int l = 1; l < levels && l < 64; ++l) {
+    off[l] = tot;
+    const size_t bytes = (size_t)x->batch * (size_t)(x->d >> l) * (size_t)(x->h >> l) *
+                         (size_t)(x->w >> l) * esz;
+    tot += (bytes + 255) & ~(size_t)255;
+  }
+  return tot;
+}
+
+int run_gen3(const haar_desc3* in, const haar_desc3* out, int levels, void* ws, size_t ws_bytes,
+             void* stream, bool fwd) {
+  size_t off[64];
+  const size_t need = ws_gen3(in, levels, off);
+  if (need && (!ws || ws_bytes < need || ((uintptr_t)ws & 255))) return HAAR_EWORKSPACE;
+  const int tin = in->dtype, tout = out->dtype;
+  const int acc = tin == HAAR_F64 ? HAAR_F64 : HAAR_F32;
+  char* wsb = static_cast<char*>(ws);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const haar_desc3* coef = fwd ? out : in;
+  const haar_desc3* img = fwd ? in : out;
+  for (int kk = 0; kk < levels; ++kk) {
+    const int l = fwd ? kk + 1 : levels - kk;  // level l: region (d, h, w) >> (l - 1)
+    Lvl3 q{};
+    q.batch = in->batch;
+    q.d = in->d >> (l - 1);
+    q.h = in->h >> (l - 1);
+    q.w = in->w >> (l - 1);
+    q.coef = coef->ptr;
+    q.c_bs = coef->batch_stride;
+    q.c_zs = coef->plane_stride;
+    q.c_rs = coef->row_stride;
+    int t_io, t_low;
+    if (l == 1) {
+      q.io = img->ptr;
+      q.i_bs = img->batch_stride;
+      q.i_zs = img->plane_stride;
+      q.i_rs = img->row_stride;
+      t_io = img->dtype;
+    } else {
+      q.io = wsb + off[l - 1];
+      q.i_rs = q.w;
+      q.i_zs = q.h * q.w;
+      q.i_bs = q.d * q.h * q.w;
+      t_io = acc;
+    }
+    if (l == levels) {
+      q.low = coef->ptr;
+      q.l_bs = coef->batch_stride;
+      q.l_zs = coef->plane_stride;
+      q.l_rs = coef->row_stride;
+      t_low = coef->dtype;
+    } else {
+      q.low = wsb + off[l];
+      q.l_rs = q.w >> 1;
+      q.l_zs = (q.h >> 1) * (q.w >> 1);
+      q.l_bs = (q.d >> 1) * (q.h >> 1) * (q.w >> 1);
+      t_low = acc;
+    }
+    const cudaError_t e = fwd ? dispatch3d_gen(true, t_io, coef->dtype, t_low, q, st)
+                              : dispatch3d_gen(false, t_low, coef->dtype, t_io, q, st);
+    if (e != cudaSuccess) {
+      set_last_cuda_error((int)e);
+      return HAAR_ECUDA;
+    }
+  }
+  return HAAR_OK;
+}
+
 int run3(const haar_desc3* in, const haar_desc3* out, int levels, void* ws, size_t ws_bytes,
          void* stream, bool fwd) {
   int rc = check3(in);
@@ -506,18 +733,13 @@ int run3(const haar_desc3* in, const haar_desc3* out, int levels, void* ws, size
   if ((tin == HAAR_F64) != (tout == HAAR_F64) || (tin != tout && tin != HAAR_F32 && tout != HAAR_F32))
     return HAAR_EDTYPE;
   if (in->batch == 0 || in->d == 0 || in->h == 0 || in->w == 0) return HAAR_OK;
-  if (in->w % 8) return HAAR_ESHAPE;  // rows are moved 8 samples at a time
   const int si = dt_size(tin), so = dt_size(tout);
-  auto al = [](const haar_desc3* d, int esz) {
-    return ((uintptr_t)d->ptr % 16) == 0 && (d->row_stride * esz) % 16 == 0 &&
-           (d->plane_stride * esz) % 16 == 0 && (d->batch_stride * esz) % 16 == 0;
-  };
-  if (!al(in, si) || !al(out, so)) return HAAR_EINVAL;
   {
     const uintptr_t a0 = (uintptr_t)in->ptr, a1 = a0 + (uintptr_t)extent3(in) * si;
     const uintptr_t b0 = (uintptr_t)out->ptr, b1 = b0 + (uintptr_t)extent3(out) * so;
     if (a0 < b1 && b0 < a1) return HAAR_EALIAS;
   }
+  if (!tiled3_ok(in, out, levels)) return run_gen3(in, out, levels, ws, ws_bytes, stream, fwd);
   int lv[64], cum[65];
   const int np = plan_passes3(levels, lv, cum);
   size_t off[64];
@@ -530,7 +752,6 @@ int run3(const haar_desc3* in, const haar_desc3* out, int levels, void* ws, size
     const int k = fwd ? kk : np - 1 - kk;
     const int s0 = cum[k], s1 = cum[k + 1];
     const int64_t dk = in->d >> s0, hk = in->h >> s0, wk = in->w >> s0;
-    if (wk % 8) return HAAR_ESHAPE;  // a deep pass on a region narrower than 8
     Pass3 p{};
     p.levels = lv[k];
     p.batch = in->batch;
@@ -595,7 +816,7 @@ int haar_workspace_size_3d(const haar_desc3* x, int levels, size_t* bytes) {
   if (rc) return rc;
   if (levels < 1 || levels > 30) return HAAR_EINVAL;
   size_t off[64];
-  *bytes = ws3(x, levels, off);
+  *bytes = tiled3_ok(x, x, levels) ? ws3(x, levels, off) : ws_gen3(x, levels, off);
   return HAAR_OK;
 }
 

@@ -288,6 +288,13 @@ def test_volume_rejections(lib):
         assert run(fn, v(A, rs=32), v(B), 1) == L.HAAR_EINVAL            # row stride < w
         assert run(fn, v(A), v(B), 4) == L.HAAR_EWORKSPACE               # deep: needs scratch
         assert run(fn, v(A, b=0), v(B, b=0), 2) == L.HAAR_OK
+        assert run(fn, v(A, w=12), v(B, w=12), 2) == L.HAAR_EWORKSPACE   # generic: low bands
+    # the workspace of the generic path: the low band of every level but the last
+    n = ctypes.c_size_t()
+    assert lib.haar_workspace_size_3d(ctypes.byref(v(A, w=12)), 2, ctypes.byref(n)) == 0
+    assert n.value == ((1 * 8 * 8 * 6 * 4 + 255) // 256) * 256
+    assert lib.haar_workspace_size_3d(ctypes.byref(v(A)), 3, ctypes.byref(n)) == 0
+    assert n.value == 0  # three levels fuse in one tiled pass
 
 
 def test_noalloc_validates_both_descriptors_before_the_scratch_size(lib):

@@ -50,6 +50,39 @@ def test_3d_fp64_and_strided():
     assert_close(cv, oracle.dwt3d(v.double().cpu().numpy(), 3), torch.float32, "dwt3d strided")
 
 
+# Volumes the tiled kernels cannot take run the generic per-level kernel:
+# widths that are not multiples of 8, a second pass narrower than 8, rows
+# that start off a 16-byte boundary; mixed storage types and fp64 too.
+GENERIC = [((1, 8, 8, 12), 2), ((2, 16, 12, 20), 2), ((1, 16, 16, 48), 4), ((1, 4, 6, 2), 1),
+           ((2, 32, 32, 36), 2)]
+
+
+@pytest.mark.parametrize("shape,levels", GENERIC)
+@pytest.mark.parametrize("dt,cdt", [(torch.float32, torch.float32), (torch.bfloat16, torch.bfloat16),
+                                    (torch.float32, torch.bfloat16), (torch.float16, torch.float32)])
+def test_3d_generic_path(shape, levels, dt, cdt):
+    x = volume(shape, seed=levels + shape[-1], dtype=dt)
+    c = api.dwt3d(x, levels, dtype=cdt)
+    xh = x.double().cpu().numpy()
+    assert_close(c, oracle.dwt3d(xh, levels), cdt if cdt != torch.float32 else dt,
+                 f"generic dwt3d {shape} L{levels}")
+    y = api.idwt3d(c, levels, dtype=dt)
+    assert_close(y, oracle.idwt3d(c.double().cpu().numpy(), levels), cdt if cdt != torch.float32 else dt,
+                 f"generic idwt3d {shape} L{levels}")
+
+
+def test_3d_generic_unaligned_and_fp64():
+    big = volume((1, 10, 18, 70), seed=6)
+    v = big[:, 1:9, 1:17, 3:67]  # 8 x 16 x 64, rows starting 12 bytes past the allocation
+    c = api.dwt3d(v, 3)
+    assert_close(c, oracle.dwt3d(v.double().cpu().numpy(), 3), torch.float32, "unaligned dwt3d")
+    y = api.idwt3d(c, 3)
+    assert_close(y, v.double().cpu().numpy(), torch.float32, "unaligned round trip")
+    x = volume((2, 8, 8, 12), seed=7, dtype=torch.float64)
+    c = api.dwt3d(x, 2)
+    assert_close(c, oracle.dwt3d(x.cpu().numpy(), 2), torch.float64, "generic fp64")
+
+
 def test_3d_constant_exact_zero_detail():
     x = torch.full((1, 16, 16, 64), 0.25, device=DEV)
     c = api.dwt3d(x, 3).cpu().numpy()[0]
@@ -62,8 +95,8 @@ def test_3d_rejections():
     st = torch.cuda.current_stream().cuda_stream
     x = torch.zeros(1, 8, 8, 12, device=DEV)
     assert lib.haar_dwt_3d(ctypes.byref(api.describe3(x)),
-                           ctypes.byref(api.describe3(torch.zeros_like(x))), 1, None, 0, st) \
-        == _lib.HAAR_ESHAPE
+                           ctypes.byref(api.describe3(torch.zeros_like(x))), 3, None, 0, st) \
+        == _lib.HAAR_ESHAPE  # 12 not divisible by 2^3
     y = torch.zeros(1, 8, 8, 64, device=DEV)
     assert lib.haar_dwt_3d(ctypes.byref(api.describe3(y)), ctypes.byref(api.describe3(y)), 1,
                            None, 0, st) == _lib.HAAR_EALIAS

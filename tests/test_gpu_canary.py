@@ -86,7 +86,9 @@ def test_1d_writes_stay_inside(rows, n, levels):
 
 
 @pytest.mark.parametrize("shape,levels", [((1, 16, 16, 64), 2), ((1, 24, 40, 72), 3),
-                                          ((2, 8, 8, 64), 3)])
+                                          ((2, 8, 8, 64), 3),
+                                          # the generic per-level path
+                                          ((1, 8, 8, 12), 2), ((2, 16, 12, 20), 2)])
 def test_3d_writes_stay_inside(shape, levels):
     x = torch.rand(shape, device=DEV)
     cb, c = guarded(shape, torch.float32)
