@@ -13,7 +13,7 @@
 //   x[2n + p] = sum_i h[p + 2i] a[n - i] + g[p + 2i] d[n - i],  i < K/2.
 //
 // Work is cut into chunks of 4096 level-0 positions (4096 / 2^l coefficients
-// at level l; 8192 for the analysis with K >= 6).  Analysis: the chunk plus
+// at level l; 8192 with K >= 6).  Analysis: the chunk plus
 // a right halo of (K - 2)(2^L - 1) samples (wrapped) is staged in shared
 // memory with asynchronous 16-byte copies and every level is fused there,
 // two levels per pass: a thread takes 8 consecutive inputs of level l, makes
@@ -33,10 +33,8 @@
 
 namespace fh {
 
-constexpr int kFChunk = 4096;  // level-0 positions per synthesis block
 constexpr int kFMaxLevels = 10;
 constexpr int kFMaxTaps = 8;
-constexpr int kFThreads = 128;   // synthesis block
 
 // Analysis chunk and block.  A chunk recomputes a right halo of
 // (K - 2)(2^L - 1) samples for its coarser levels, so the longer filters
@@ -45,6 +43,14 @@ template <int K>
 __host__ __device__ constexpr int fchunk_a() { return K >= 6 ? 8192 : 4096; }
 template <int K>
 __host__ __device__ constexpr int fthreads_a() { return K >= 6 ? 256 : 128; }
+// Synthesis chunk (level-0 positions per block) and block.  The passes
+// over the coarse levels, the windows' left extensions and the per-block
+// set-up are the same for every chunk, so the longer filters, whose passes
+// cost the most, take chunks twice as long (the same 32 outputs per thread).
+template <int K>
+__host__ __device__ constexpr int fchunk_s() { return K >= 6 ? 8192 : 4096; }
+template <int K>
+__host__ __device__ constexpr int fthreads_s() { return K >= 6 ? 256 : 128; }
 
 struct FilterArgs {
   const void* in;
@@ -86,7 +92,7 @@ __host__ __device__ constexpr int fdwt_cap_b(int L) {
 // room for the 8-wide reads of level 1 past its end
 template <typename T, int K>
 __host__ __device__ constexpr int fidwt_seg_cap(int l) {
-  return fround((kFChunk >> l) + 2 * (K / 2 - 1) + 2 + 2 * fvec<T>() + 8, fvec<T>());
+  return fround((fchunk_s<K>() >> l) + 2 * (K / 2 - 1) + 2 + 2 * fvec<T>() + 8, fvec<T>());
 }
 template <typename T, int K>
 __host__ __device__ constexpr int fidwt_stage_cap(int L) {
@@ -99,11 +105,11 @@ __host__ __device__ constexpr int fidwt_stage_cap(int L) {
 // the 8 values a unit writes past it and the reads past it
 template <typename T, int K>
 __host__ __device__ constexpr int fidwt_big_cap() {
-  return fround((kFChunk >> 2) + 4 * (K / 2 - 1) + 16 + 2 * fvec<T>(), fvec<T>());
+  return fround((fchunk_s<K>() >> 2) + 4 * (K / 2 - 1) + 16 + 2 * fvec<T>(), fvec<T>());
 }
 template <typename T, int K>
 __host__ __device__ constexpr int fidwt_small_cap() {
-  return fround((kFChunk >> 4) + 4 * (K / 2 - 1) + 16 + 2 * fvec<T>(), fvec<T>());
+  return fround((fchunk_s<K>() >> 4) + 4 * (K / 2 - 1) + 16 + 2 * fvec<T>(), fvec<T>());
 }
 // e_l of the synthesis window start lo(l) = (m0 >> l) - e_l: e_0 = 0,
 // e_l = ceil(e_{l-1} / 2) + K/2 - 1 (the same for every chunk)
@@ -256,6 +262,70 @@ __device__ __forceinline__ void dwt_pair_rc(const T* X, T* lo, T* d1, T* d2, int
   }
 }
 
+// The arithmetic of one unit on every lane of the warp: 4 outputs of level
+// l + 1 from the lane's inputs xs[0, K + 6), the K - 2 after them from the
+// next lanes, then 2 of level l + 2.  Without DETAILS only the low-pass
+// outputs are made.
+template <typename T, int K, bool DETAILS>
+__device__ __forceinline__ void sh_unit(const T* xs, const T* h, const T* g, T (&e1)[4],
+                                        T (&a2)[2], T (&e2)[2]) {
+  using VT = typename FVec16<T>::type;
+  constexpr int V = fvec<T>();
+  constexpr int NW = (K + 6 + V - 1) / V;  // 16-byte loads per unit
+  T x[NW * V];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) *reinterpret_cast<VT*>(x + i * V) = reinterpret_cast<const VT*>(xs)[i];
+  T a1[K + 2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) s = fma(h[k], x[2 * j + k], s);
+    a1[j] = s;
+  }
+  if constexpr (DETAILS) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s = fma(g[k], x[2 * j + k], s);
+      e1[j] = s;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K - 2; ++j) a1[4 + j] = __shfl_down_sync(0xffffffffu, a1[j % 4], 1 + j / 4);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) s = fma(h[k], a1[2 * j + k], s);
+    a2[j] = s;
+  }
+  if constexpr (DETAILS) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      T d = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) d = fma(g[k], a1[2 * j + k], d);
+      e2[j] = d;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void put_unit(T* d1, T* d2, T* lo, const T (&e1)[4], const T (&a2)[2],
+                                         const T (&e2)[2]) {
+  using V2 = typename FVec2<T>::type;
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(d1) = make_float4(e1[0], e1[1], e1[2], e1[3]);
+  } else {
+    *reinterpret_cast<V2*>(d1) = V2{e1[0], e1[1]};
+    *reinterpret_cast<V2*>(d1 + 2) = V2{e1[2], e1[3]};
+  }
+  *reinterpret_cast<V2*>(d2) = V2{e2[0], e2[1]};
+  *reinterpret_cast<V2*>(lo) = V2{a2[0], a2[1]};
+}
+
 // Two levels in one pass, a warp at a time (the form for K >= 6, where the
 // values made twice above are most of the work).  X holds this level's
 // input: len samples of the chunk and a right halo r; m2 = len/4 + r2
@@ -269,85 +339,55 @@ __device__ __forceinline__ void dwt_pair_rc(const T* X, T* lo, T* d1, T* d2, int
 // Outputs past the ends (m2, len/2, len/4) come from the buffer's slack and
 // are not stored; lanes past the last unit read as the R-th lane after it,
 // so reads end at X[len + r + 9], inside the 16 elements of slack every
-// staging buffer has.  Units u < len/8 have all their outputs inside: with
-// VEC (every output vector aligned) a pass of such units stores whole
-// vectors without guards.
+// staging buffer has.
+//
+// With VEC (every output vector aligned) the passes whose units all lie
+// inside the chunk (base + W <= len/8) run first in a loop of their own:
+// no clamp (lanes W.. read unit len/8 + R - 1 at most, and U >= len/8), the
+// details kept, whole-vector stores without guards, and addresses that
+// advance by a fixed stride.  The remaining passes (halo units, whose only
+// stored outputs are a_{l+2}, and a ragged end) check each store.
 template <typename T, int K, int NT, bool VEC>
 __device__ __forceinline__ void dwt_pair_sh(const T* X, T* lo, T* d1, T* d2, int len, int m2,
                                             const T* h, const T* g, int tid) {
-  using VT = typename FVec16<T>::type;
-  using V2 = typename FVec2<T>::type;
-  constexpr int V = fvec<T>();
   constexpr int R = (K - 2 + 3) / 4;
   constexpr int W = 32 - R;
-  constexpr int NW = (K + 6 + V - 1) / V;  // 16-byte loads per unit
+  constexpr int S = (NT / 32) * W;  // units one pass of the block covers
   const int lane = tid & 31;
   const int U = (m2 + 1) / 2, n1 = len >> 1, n2 = len >> 2;
-  const int nfull = VEC ? len >> 3 : 0;
-  for (int base = (tid >> 5) * W; base < U; base += (NT / 32) * W) {
+  int base = (tid >> 5) * W;
+  if constexpr (VEC) {
+    const int nfull = len >> 3;
+    const T* xs = X + 8 * (base + lane);
+    T* d1p = d1 + 4 * (base + lane);
+    T* d2p = d2 + 2 * (base + lane);
+    T* lop = lo + 2 * (base + lane);
+    for (; base + W <= nfull; base += S) {
+      T e1[4], a2[2], e2[2];
+      sh_unit<T, K, true>(xs, h, g, e1, a2, e2);
+      if (lane < W) put_unit(d1p, d2p, lop, e1, a2, e2);
+      xs += 8 * S;
+      d1p += 4 * S;
+      d2p += 2 * S;
+      lop += 2 * S;
+    }
+  }
+  for (; base < U; base += S) {
     const int u = base + lane;
-    const int ur = min(u, U - 1 + R);
-    T x[NW * V];
-#pragma unroll
-    for (int i = 0; i < NW; ++i)
-      *reinterpret_cast<VT*>(x + i * V) = reinterpret_cast<const VT*>(X + 8 * ur)[i];
+    const T* xs = X + 8 * min(u, U - 1 + R);
+    T e1[4] = {}, a2[2], e2[2] = {};
     // a pass past len/8 units keeps no details (halo units feed the coarser
     // levels' low-pass outputs only); the same for the whole warp
-    const bool details = 4 * base < n1;
-    T a1[K + 2], e1[4] = {}, e2[2] = {}, a2[2];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < K; ++k) s = fma(h[k], x[2 * j + k], s);
-      a1[j] = s;
-    }
-    if (details) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        T s = T(0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) s = fma(g[k], x[2 * j + k], s);
-        e1[j] = s;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < K - 2; ++j) a1[4 + j] = __shfl_down_sync(0xffffffffu, a1[j % 4], 1 + j / 4);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < K; ++k) s = fma(h[k], a1[2 * j + k], s);
-      a2[j] = s;
-    }
-    if (details) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        T d = T(0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) d = fma(g[k], a1[2 * j + k], d);
-        e2[j] = d;
-      }
-    }
+    if (4 * base < n1) sh_unit<T, K, true>(xs, h, g, e1, a2, e2);
+    else sh_unit<T, K, false>(xs, h, g, e1, a2, e2);
     if (lane < W) {
-      if (base + W <= nfull) {
-        if constexpr (sizeof(T) == 4) {
-          *reinterpret_cast<float4*>(d1 + 4 * u) = make_float4(e1[0], e1[1], e1[2], e1[3]);
-        } else {
-          *reinterpret_cast<V2*>(d1 + 4 * u) = V2{e1[0], e1[1]};
-          *reinterpret_cast<V2*>(d1 + 4 * u + 2) = V2{e1[2], e1[3]};
-        }
-        *reinterpret_cast<V2*>(d2 + 2 * u) = V2{e2[0], e2[1]};
-        *reinterpret_cast<V2*>(lo + 2 * u) = V2{a2[0], a2[1]};
-      } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (4 * u + i < n1) d1[4 * u + i] = e1[i];
+      for (int i = 0; i < 4; ++i)
+        if (4 * u + i < n1) d1[4 * u + i] = e1[i];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          if (2 * u + i < n2) d2[2 * u + i] = e2[i];
-          if (2 * u + i < m2) lo[2 * u + i] = a2[i];
-        }
+      for (int i = 0; i < 2; ++i) {
+        if (2 * u + i < n2) d2[2 * u + i] = e2[i];
+        if (2 * u + i < m2) lo[2 * u + i] = a2[i];
       }
     }
   }
@@ -569,7 +609,7 @@ __device__ __forceinline__ void idwt_pair(const T* Aw, const T* Dw, const T* Dw1
 }
 
 // 8 consecutive output values at a unit's start, whose alignment is that of
-// the chunk start (units are 8 values, chunks 4096): one 256-bit store (AL =
+// the chunk start (units are 8 values, chunks 4096 or 8192): one 256-bit store (AL =
 // 32), 16-byte stores (AL = 16) or element stores (AL = 0).
 template <typename T, int AL>
 __device__ __forceinline__ void put8(T* p, const T (&y)[8]) {
@@ -699,10 +739,10 @@ __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, int
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
+__global__ void __launch_bounds__(fthreads_s<K>()) k_filter_idwt(const FilterArgs a) {
+  constexpr int V = fvec<T>(), CH = fchunk_s<K>(), NT = fthreads_s<K>();
   pdl_wait();
   pdl_trigger();
-  constexpr int V = fvec<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.levels;
   T* S = reinterpret_cast<T*>(smem_raw);
@@ -716,9 +756,9 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
     g[k] = param<T>(a.g[k], a.gf[k]);
   }
   const unsigned chunks = (unsigned)a.chunks;
-  const int64_t row = blockIdx.x / chunks, m0 = (int64_t)(blockIdx.x % chunks) * kFChunk;
+  const int64_t row = blockIdx.x / chunks, m0 = (int64_t)(blockIdx.x % chunks) * CH;
   const int64_t n = a.n;
-  const int C = (int)min((int64_t)kFChunk, n - m0);
+  const int C = (int)min((int64_t)CH, n - m0);
   const int64_t end = m0 + C;
   const T* c = static_cast<const T*>(a.in) + row * n;
   T* x = static_cast<T*>(a.out) + row * n;
@@ -726,7 +766,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   // offset the host computed, then one wait for everything
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int w = warp; w <= L; w += kFThreads / 32) {
+    for (int w = warp; w <= L; w += NT / 32) {
       const int l = w == 0 ? L : L + 1 - w;
       const int64_t nl = n >> l, s = (m0 >> l) - a.e[l];
       stage<32>(S + a.woff[w], w == 0 ? c : c + nl, nl, s, (int)((end >> l) - s), lane);
@@ -740,9 +780,9 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   };
   if (L == 1) {
     const T *A1 = S + a.woff[0], *D1 = S + a.woff[1];
-    if (al == 32) idwt_level1<T, K, kFThreads, 32>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
-    else if (al == 16) idwt_level1<T, K, kFThreads, 16>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
-    else idwt_level1<T, K, kFThreads, 0>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    if (al == 32) idwt_level1<T, K, NT, 32>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else if (al == 16) idwt_level1<T, K, NT, 16>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
+    else idwt_level1<T, K, NT, 0>(A1, D1, x + m0, C >> 1, h, g, threadIdx.x);
     return;
   }
   // passes of at most 64 units run on warp 0 alone; the block waits for
@@ -768,7 +808,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
       idwt_level<T, K, 32>(Aw, win(L), B, np, h, g, threadIdx.x);
       __syncwarp();
     } else if (ph == 2) {
-      idwt_level<T, K, kFThreads>(Aw, win(L), B, np, h, g, threadIdx.x);
+      idwt_level<T, K, NT>(Aw, win(L), B, np, h, g, threadIdx.x);
       __syncthreads();
     }
     Aw = B + (em & 1);
@@ -787,9 +827,9 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
         __syncwarp();
       } else {
         if (odd)
-          idwt_pair<T, K, kFThreads, true>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
+          idwt_pair<T, K, NT, true>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
         else
-          idwt_pair<T, K, kFThreads, false>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
+          idwt_pair<T, K, NT, false>(Aw, win(l), win(l - 1), B, units, h, g, threadIdx.x);
         __syncthreads();
       }
     }
@@ -800,19 +840,19 @@ __global__ void __launch_bounds__(kFThreads) k_filter_idwt(const FilterArgs a) {
   if (L == 2) {
     const T *Ab = S + a.woff[0], *D2 = S + a.woff[1], *D1 = S + a.woff[2];
     if (al == 32)
-      idwt_pair_last<T, K, kFThreads, true, 32>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+      idwt_pair_last<T, K, NT, true, 32>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
     else if (al == 16)
-      idwt_pair_last<T, K, kFThreads, true, 16>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+      idwt_pair_last<T, K, NT, true, 16>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
     else
-      idwt_pair_last<T, K, kFThreads, true, 0>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+      idwt_pair_last<T, K, NT, true, 0>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
   } else {
     const T *Ab = P(2), *D2 = S + a.woff[L - 1], *D1 = S + a.woff[L];
     if (al == 32)
-      idwt_pair_last<T, K, kFThreads, false, 32>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+      idwt_pair_last<T, K, NT, false, 32>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
     else if (al == 16)
-      idwt_pair_last<T, K, kFThreads, false, 16>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+      idwt_pair_last<T, K, NT, false, 16>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
     else
-      idwt_pair_last<T, K, kFThreads, false, 0>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
+      idwt_pair_last<T, K, NT, false, 0>(Ab, D2, D1, x + m0, C >> 1, h, g, threadIdx.x);
   }
 }
 
@@ -825,7 +865,7 @@ size_t filter_smem(bool fwd, int L) {
 
 template <typename T, int K>
 cudaError_t filter_launch_k(bool fwd, FilterArgs a, cudaStream_t s) {
-  const int chunk = fwd ? fchunk_a<K>() : kFChunk;
+  const int chunk = fwd ? fchunk_a<K>() : fchunk_s<K>();
   a.chunks = (a.n + chunk - 1) / chunk;
   const int64_t total = a.rows * a.chunks;
   if (total == 0) return cudaSuccess;
@@ -836,7 +876,7 @@ cudaError_t filter_launch_k(bool fwd, FilterArgs a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)total);
-  cfg.blockDim = dim3(fwd ? fthreads_a<K>() : kFThreads);
+  cfg.blockDim = dim3(fwd ? fthreads_a<K>() : fthreads_s<K>());
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
