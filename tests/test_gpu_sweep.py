@@ -121,3 +121,66 @@ def test_sweep_filter_bank(i, K, rows, n, L, dt, off):
     y = api.filter_idwt1d(c, L, h)
     yref = oracle.filter_idwt1d(host64(c), L, np.array(h))
     assert_close(y, yref, dt, f"sweep K-tap synthesis {i} (K={K})")
+
+
+def cases_3d(count=40, seed=31337):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        L = int(rng.integers(1, 5))
+        d, h, w = ((1 << L) * int(rng.integers(1, 1 + max(1, 48 >> L))) for _ in range(3))
+        b = int(rng.integers(1, 3))
+        dt = DTYPES[int(rng.integers(0, 3))]
+        pad = int(rng.choice([0, 8, 3]))  # row padding; 3 breaks the tiled kernels' alignment
+        out.append((i, b, d, h, w, L, dt, pad))
+    return out
+
+
+@pytest.mark.parametrize("i,b,d,h,w,L,dt,pad", cases_3d())
+def test_sweep_3d(i, b, d, h, w, L, dt, pad):
+    """Volumes of every side mix, padded rows (some breaking the tiles'
+    alignment, which moves them to the per-level kernels)."""
+    g = torch.Generator(device="cpu").manual_seed(4000 + i)
+    vals = (torch.rand(b, d, h, w, generator=g, dtype=torch.float64) * 4 - 2).to(dt).to(DEV)
+    x = padded_view(vals, 0, pad)
+    c = api.dwt3d(x, L)
+    assert_close(c, oracle.dwt3d(host64(x), L), dt, f"sweep 3D analysis {i}")
+    y = padded_view(torch.zeros(b, d, h, w, dtype=dt, device=DEV), 0, pad)
+    api.idwt3d(c, L, out=y)
+    assert_close(y, oracle.idwt3d(host64(c), L), dt, f"sweep 3D synthesis {i}")
+
+
+def cases_shrink(count=40, seed=99):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        two_d = bool(rng.integers(0, 2))
+        L = int(rng.integers(1, 6 if two_d else 9))
+        if two_d:
+            shape = (int(rng.integers(1, 3)), 32 * int(rng.integers(1, 9)),
+                     32 * int(rng.integers(1, 9)))
+        else:
+            shape = (int(rng.integers(1, 5)), 256 * int(rng.integers(1, 17)))
+        dt = (torch.float32, torch.float64)[int(rng.integers(0, 2))]
+        t = float(rng.choice([0.0, 0.05, 0.3, 1.0]))
+        pad = int(rng.choice([0, 8]))  # 16-byte aligned rows, padded or not
+        out.append((i, two_d, shape, L, dt, t, pad))
+    return out
+
+
+@pytest.mark.parametrize("i,two_d,shape,L,dt,t,pad", cases_shrink())
+def test_sweep_soft_shrinkage(i, two_d, shape, L, dt, t, pad):
+    """One-pass soft shrinkage (continuous in the coefficients, so no
+    threshold decision to match) against the oracle's analysis, shrink and
+    synthesis."""
+    g = torch.Generator(device="cpu").manual_seed(5000 + i)
+    vals = (torch.rand(*shape, generator=g, dtype=torch.float64) * 4 - 2).to(dt).to(DEV)
+    x = padded_view(vals, 0, pad)
+    y = padded_view(torch.zeros(*shape, dtype=dt, device=DEV), 0, pad)
+    if two_d:
+        api.denoise2d(x, L, t, out=y)
+        ref = oracle.denoise2d(host64(x), L, t)
+    else:
+        api.denoise1d(x, L, t, out=y)
+        ref = oracle.denoise1d(host64(x), L, t)
+    assert_close(y, ref, dt, f"sweep shrinkage {i} ({'2D' if two_d else '1D'}, t={t})")
