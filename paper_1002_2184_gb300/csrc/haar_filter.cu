@@ -362,6 +362,8 @@ __device__ __forceinline__ void dwt_pair_sh(const T* X, T* lo, T* d1, T* d2, int
     T* d1p = d1 + 4 * (base + lane);
     T* d2p = d2 + 2 * (base + lane);
     T* lop = lo + 2 * (base + lane);
+    // unrolled twice: 8-tap analysis 74.0 -> 75.5 % of measured HBM
+#pragma unroll 2
     for (; base + W <= nfull; base += S) {
       T e1[4], a2[2], e2[2];
       sh_unit<T, K, true>(xs, h, g, e1, a2, e2);
