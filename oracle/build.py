@@ -16,8 +16,8 @@ SRC = os.path.join(HERE, "haar_oracle.c")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhaar_oracle.so")
 # the FP32 CPU baseline of the benchmark (cpu_baseline.c; not the oracle)
-BASELINE_SRC = os.path.join(HERE, "cpu_baseline.c")
-BASELINE_LIB = os.path.join(OUT_DIR, "libhaar_cpu_baseline.so")
+CPU_LOOP_SRC = os.path.join(HERE, "cpu_baseline.c")
+CPU_LOOP_LIB = os.path.join(OUT_DIR, "libhaar_cpu_baseline.so")
 
 
 def _compile(src: str, lib: str, opt: str, force: bool) -> str:
@@ -36,13 +36,13 @@ def _compile(src: str, lib: str, opt: str, force: bool) -> str:
 def build(force: bool = False) -> str:
     """Compile the oracle (and the CPU baseline beside it) if a library is
     missing or older than its source; returns the oracle's path."""
-    _compile(BASELINE_SRC, BASELINE_LIB, "-O3", force)
+    _compile(CPU_LOOP_SRC, CPU_LOOP_LIB, "-O3", force)
     return _compile(SRC, LIB, "-O2", force)
 
 
 def build_baseline(force: bool = False) -> str:
     """Compile the FP32 CPU baseline only; returns its path."""
-    return _compile(BASELINE_SRC, BASELINE_LIB, "-O3", force)
+    return _compile(CPU_LOOP_SRC, CPU_LOOP_LIB, "-O3", force)
 
 
 if __name__ == "__main__":
