@@ -28,6 +28,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// Before a kernel's dependency wait: ask L2 for `bytes` from p, one 128-byte
+// line per thread in turn (a hint only: the loads after the wait see every
+// earlier write), so that a launch's first reads overlap the previous
+// launch's drain.  NT threads share the lines.
+template <int NT>
+__device__ __forceinline__ void warm_l2(const void* p, int64_t bytes, int tid) {
+  const char* c = static_cast<const char*>(p);
+  for (int64_t o = (int64_t)tid * 128; o < bytes; o += (int64_t)NT * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o) : "memory");
+}
+
 // Copy n elements from src to dst, both 16-byte aligned, as ceil(n / V)
 // 16-byte pieces shared by NT threads (one 32-bit shared and one global
 // address, both advanced per copy).

@@ -422,6 +422,16 @@ __device__ __forceinline__ void dwt_pair_step(const T* X, T* Y, T* out, T* d1, T
 template <typename T, int K>
 __global__ void __launch_bounds__(fthreads_a<K>()) k_filter_dwt(const FilterArgs a) {
   constexpr int NT = fthreads_a<K>(), CH = fchunk_a<K>();
+  {
+    // before the dependency wait, ask L2 for the chunk and its right halo
+    // (up to the row's end; 64 x 2^20 fp32, 8 levels: Daubechies-4
+    // analysis 97 -> 99 %, 8 taps 75.5 -> 77 % of measured HBM)
+    const unsigned ch = (unsigned)a.chunks;
+    const int64_t rw = blockIdx.x / ch, kk = (int64_t)(blockIdx.x % ch) * CH;
+    const int64_t end = min(a.n, kk + CH + (K - 2) * ((1 << a.levels) - 1));
+    warm_l2<NT>(static_cast<const T*>(a.in) + rw * a.n + kk, (end - kk) * (int64_t)sizeof(T),
+                threadIdx.x);
+  }
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -743,6 +753,18 @@ __device__ __forceinline__ void idwt_level1(const T* A1, const T* D1, T* xo, int
 template <typename T, int K>
 __global__ void __launch_bounds__(fthreads_s<K>()) k_filter_idwt(const FilterArgs a) {
   constexpr int V = fvec<T>(), CH = fchunk_s<K>(), NT = fthreads_s<K>();
+  {
+    const unsigned ch = (unsigned)a.chunks;
+    const int64_t rw = blockIdx.x / ch, mm = (int64_t)(blockIdx.x % ch) * CH;
+    const int64_t cc = min((int64_t)CH, a.n - mm);
+    const T* cr = static_cast<const T*>(a.in) + rw * a.n;
+    // before the dependency wait, ask L2 for the chunk's d_1 and d_2 (three
+    // quarters of what the block reads; Daubechies-4 synthesis 96 -> 98 %,
+    // 6 taps 89 -> 92 %)
+    warm_l2<NT>(cr + (a.n >> 1) + (mm >> 1), (cc >> 1) * (int64_t)sizeof(T), threadIdx.x);
+    if (a.levels >= 2)
+      warm_l2<NT>(cr + (a.n >> 2) + (mm >> 2), (cc >> 2) * (int64_t)sizeof(T), threadIdx.x);
+  }
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];

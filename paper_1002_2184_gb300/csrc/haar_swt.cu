@@ -43,17 +43,19 @@ __host__ __device__ constexpr int swt_cap() {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_swt(const SwtArgs a) {
+  const unsigned chunks = (unsigned)a.chunks;
+  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kSwtChunk;
+  const int64_t n = a.n;
+  const int C = (int)min((int64_t)kSwtChunk, n - k0);
+  const T* x = static_cast<const T*>(a.in) + row * n;
+  // the chunk's input (1D, 64 x 2^20, one level: 98 -> 102 % of measured HBM)
+  warm_l2<256>(x + k0, (int64_t)C * sizeof(T), threadIdx.x);
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + swt_cap<T>();
-  const unsigned chunks = (unsigned)a.chunks;
-  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kSwtChunk;
-  const int64_t n = a.n;
-  const int C = (int)min((int64_t)kSwtChunk, n - k0);
   const int H = (1 << a.levels) - 1;
-  const T* x = static_cast<const T*>(a.in) + row * n;
   T* out = static_cast<T*>(a.out) + row * (a.levels + 1) * n;
   stage<256>(A, x, n, k0, C + H, threadIdx.x);  // k0 is 16-byte aligned: no shift
   cp_async_wait_all();
@@ -78,17 +80,20 @@ __global__ void __launch_bounds__(256) k_swt(const SwtArgs a) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_iswt(const SwtArgs a) {
+  const unsigned chunks = (unsigned)a.chunks;
+  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kSwtChunk;
+  const int64_t n = a.n;
+  const int C = (int)min((int64_t)kSwtChunk, n - k0);
+  const T* c = static_cast<const T*>(a.in) + row * (a.levels + 1) * n;
+  // the chunk's part of every coefficient row (one level: 90 -> 91 %)
+  for (int l = 0; l <= a.levels; ++l)
+    warm_l2<256>(c + (int64_t)l * n + k0, (int64_t)C * sizeof(T), threadIdx.x);
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + swt_cap<T>();
   T* bufD = bufB + swt_cap<T>();
-  const unsigned chunks = (unsigned)a.chunks;
-  const int64_t row = blockIdx.x / chunks, k0 = (int64_t)(blockIdx.x % chunks) * kSwtChunk;
-  const int64_t n = a.n;
-  const int C = (int)min((int64_t)kSwtChunk, n - k0);
-  const T* c = static_cast<const T*>(a.in) + row * (a.levels + 1) * n;
   T* x = static_cast<T*>(a.out) + row * n;
   const int L = a.levels;
   int H = (1 << L) - 1;  // left halo of a_L
